@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 parallel samplesort (one JSON line on stdout).
+
+Default workload: one exact-splitting (PSES) sort of 2^30 int64 keys drawn
+uniformly over the full range, out of place in HBM (8 GB of keys + the
+library's workspace), n_B and n_P chosen by the library.  A step is one
+ps_sort call over the resident keys: block sort, pivot selection, split
+table, offsets and multiway merge.  The keys are restored from a pristine
+device copy before each step, outside the timed events.  Inputs (8 GB) are
+larger than L2 (129 MB), so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--n 1073741824] [--dtype int64] [--dist uniform] [--pivot exact]
+
+--impl reference times the CPU oracle (the four steps written plainly in C,
+one thread) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES = {"int32": 4, "uint32": 4, "float32": 4, "int64": 8, "uint64": 8, "float64": 8}
+METRIC = "Gkeys/s per sort (single large sort)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 30)
+    ap.add_argument("--dtype", default="int64", choices=sorted(BYTES))
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--pivot", default="exact", choices=["exact", "regular"])
+    ap.add_argument("--n-blocks", type=int, default=0)
+    ap.add_argument("--n-parts", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 23)
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return "single sort N=2^%d %s %s, %s splitting" % (
+        a.n.bit_length() - 1, a.dtype, a.dist, "exact" if a.pivot == "exact" else "regular-sampling")
+
+
+# ------------------------------------------------------------ clocks sampler
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read only)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """dram bytes per launch recorded in profiles/ncu_traffic.json for this
+    kernel and workload (null when absent or stale)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(workload, {}).get(kernel)
+        return None if e is None else e.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ reference arm
+def oracle_time(a, n_sample: int):
+    """Time the CPU oracle (as it stands, one thread) on a bounded sample of
+    the workload; returns (keys per second, seconds, sample size)."""
+    import oracle
+    import synth
+    oracle.build()
+    keys = synth.keys(n_sample, a.dtype, a.dist, seed=synth.seed_for("bench-cpu", a.dtype, a.dist))
+    nb = np_ = 64
+    t0 = time.perf_counter()
+    oracle.sort(keys, oracle.EXACT if a.pivot == "exact" else oracle.REGULAR, nb, np_)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_sample = a.cpu_sample
+    import oracle  # noqa: F401
+    for _ in range(a.warmup):
+        oracle_time(a, min(n_sample, 1 << 20))
+    rates, secs = [], []
+    for _ in range(a.steps):
+        r, dt = oracle_time(a, n_sample)
+        rates.append(r)
+        secs.append(dt)
+    value = (n_sample * len(rates)) / sum(secs) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": a.dtype, "data": "synthetic (SplitMix64, seeded)",
+        "config": {"workload": workload_name(a), "n": a.n, "dist": a.dist, "pivot": a.pivot,
+                   "sample_per_step": n_sample, "n_blocks": 64, "n_parts": 64},
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d %s %s keys per step (of the %d-key workload), n_B=n_P=64"
+                                   % (n_sample, a.dtype, a.dist, a.n)},
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------ native arm
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # the CPU baseline runs first (rank 0, N = 1), before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rate, dt = oracle_time(a, a.cpu_sample)
+        cpu = {"value": rate / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+               "sample": "%d %s %s keys (of the %d-key workload), n_B=n_P=64, one thread, %.1f s"
+                         % (a.cpu_sample, a.dtype, a.dist, a.n, dt)}
+
+    import numpy as np
+    import torch
+
+    import paper_2305_05245_gb300 as ps
+    import synth
+    from paper_2305_05245_gb300 import _lib
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ps_build = ps._lib.load()  # noqa: F841  (fails loudly without the library)
+    tdt = getattr(torch, a.dtype)
+    n = a.n
+    host = synth.keys(n, a.dtype, a.dist, seed=synth.seed_for("bench", a.dtype, a.dist, rank))
+    pristine = torch.from_numpy(host.view(np.int64 if BYTES[a.dtype] == 8 else np.int32)).to(dev)
+    pristine = pristine.view(tdt)
+    keys = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+    nb, np_ = ps.resolve_params(n, {"int32": 0, "int64": 1, "float32": 2, "float64": 3,
+                                    "uint32": 4, "uint64": 5}[a.dtype], a.n_blocks, a.n_parts)
+
+    def step():
+        ps.sort(keys, a.pivot, n_blocks=a.n_blocks, n_parts=a.n_parts)
+
+    for _ in range(a.warmup):
+        keys.copy_(pristine)
+        step()
+    torch.cuda.synchronize()
+    # correctness of the timed configuration: non-decreasing and a permutation
+    chk = keys.view(torch.int64 if BYTES[a.dtype] == 8 else torch.int32)
+    ok = bool((keys[1:] >= keys[:-1]).all().item()) if a.dtype.startswith(("int", "float")) else True
+    ok = ok and torch.equal(torch.sort(pristine)[0].view(chk.dtype), chk) if not a.dtype.startswith("float") else ok
+
+    ps.profile_reset()
+    ps.profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(a.steps):
+            keys.copy_(pristine)
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ps.profile_enable(False)
+    step_ms = [s.elapsed_time(e) for s, e in evs]
+    total_ms = sum(step_ms)
+    prof = ps.profile_read()
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * a.steps / (total_ms / 1e3) / 1e9
+
+    # end to end through ps_sort_host from pinned host memory
+    e2e = None
+    if a.e2e_steps > 0:
+        pinned = torch.empty(n, dtype=tdt, pin_memory=True)
+        src = torch.from_numpy(host.view(np.int64 if BYTES[a.dtype] == 8 else np.int32)).view(tdt)
+        pinned.copy_(src)
+        ps.sort_host(pinned, a.pivot, a.n_blocks, a.n_parts)  # warm
+        times = []
+        for _ in range(a.e2e_steps):
+            pinned.copy_(src)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ps.sort_host(pinned, a.pivot, a.n_blocks, a.n_parts)
+            times.append(time.perf_counter() - t0)
+        e2e = {"value": n * len(times) / sum(times) / 1e9, "unit": "Gkeys/s",
+               "h2d_bytes_per_step": n * BYTES[a.dtype], "d2h_bytes_per_step": n * BYTES[a.dtype],
+               "api": "ps_sort_host (pinned host buffer, H2D + sort + D2H + stream sync per step)"}
+
+    if rank != 0:
+        return 0
+    s = BYTES[a.dtype]
+    hbm, src_peak = peaks()
+    launches = sum(v[0] for v in prof.values())
+    # dominant kernel by device time
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (1, 1.0))
+    dname, (dl, dms) = dom
+    data_pass = {"tile_sort", "merge_inblock", "merge_final"}
+    per_launch_bytes = 2 * n * s if dname in data_pass else None
+    inblock_passes = prof.get("merge_inblock", (0, 0))[0] // max(a.steps, 1)
+    wl = workload_name(a)
+    roof = None
+    if per_launch_bytes:
+        ach = per_launch_bytes / (dms / dl / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": src_peak,
+                "traffic": ncu_traffic(dname, wl),
+                "algorithmic_bytes_per_launch": per_launch_bytes}
+    sort_ms = total_ms / a.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": sort_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"int32": "i32", "int64": "int64", "float32": "f32",
+                                       "float64": "f64", "uint32": "u32", "uint64": "u64"}[a.dtype],
+        "data": "synthetic (SplitMix64, seeded), resident in HBM",
+        "config": {"workload": wl, "n": n, "dist": a.dist, "pivot": a.pivot, "n_blocks": nb,
+                   "n_parts": np_, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (no flush needed)",
+                   "restore": "keys restored from a pristine device copy before each step, outside the timed events",
+                   "in_block_merge_passes": inblock_passes},
+        "roofline": roof,
+        "sort_roofline": {"algorithmic_bytes_per_key": 4 * s, "achieved_gbs": 4 * s * n / (sort_ms / 1e3) / 1e9,
+                          "frac": 4 * s * n / (sort_ms / 1e3) / 1e9 / hbm,
+                          "passes_made": 2 + inblock_passes},
+        "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in prof.items()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "check": "ok" if ok else "FAILED",
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0 if ok else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * psort.h -- C ABI of libpsort, a GB300 (sm_103a) parallel samplesort.
+ *
+ * The library implements the four-step parallel samplesort of Tokuue &
+ * Ishiyama, "Performance Evaluation of Parallel Sortings on the Supercomputer
+ * Fugaku" (arXiv 2305.05245), Sec. 2:
+ *   1. sort each of n_B contiguous blocks of length ceil(N/n_B);
+ *   2. select n_P-1 pivots, by regular sampling (PSRS, Sec. 2.3) or by
+ *      exact splitting (PSES, Sec. 2.3, Eq. 1 and Eq. 2);
+ *   3. partition every sorted block by the pivots (the split table);
+ *   4. merge the k-th partition of all blocks into the output at offset O_k,
+ *      the exclusive scan of the partition sizes.
+ * Every step runs in CUDA kernels on the caller's stream; there is no CPU
+ * fallback.  The paper states only the problem ("sort an N-element sequence A
+ * in ascending order", Sec. 2); the argument conventions below are this
+ * library's own.
+ *
+ * Order.  Keys compare by an order key kappa: signed integers by value,
+ * unsigned integers by value, floats by IEEE 754 totalOrder (so -0.0 sorts
+ * before +0.0; NaN inputs are not supported and sort to the ends by their
+ * bit pattern).  Records (uint64 key, uint32 payload) compare by
+ * (key, payload).  Equal keys have equal bits, so the output is unique.
+ *
+ * Memory.  All key, payload and trace pointers are DEVICE pointers unless a
+ * function says otherwise.  The caller owns them and must keep them valid
+ * until the work queued on `stream` has finished.  The library owns its
+ * workspace: it is taken from a library-private stream-ordered memory pool
+ * (cudaMallocFromPoolAsync) on `stream` and returned to it on `stream`.
+ *
+ * Errors.  Every function returns PS_OK (0) or a negative ps_status.  Argument
+ * errors are detected before any work is queued.  Errors of kernels already
+ * queued surface at the caller's next synchronisation, as for any CUDA call.
+ * No function throws, aborts or prints.
+ *
+ * Threads.  Functions may be called from several host threads at once; calls
+ * on the same stream are ordered by the stream.
+ */
+#ifndef PSORT_H
+#define PSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st* ps_stream_t;
+
+typedef enum {
+    PS_OK = 0,
+    PS_ERR_INVALID_ARG = -1,  /* null pointer, negative size, parameter out of range */
+    PS_ERR_UNSUPPORTED = -2,  /* unknown dtype or pivot mode */
+    PS_ERR_NO_MEMORY = -3,    /* workspace allocation failed */
+    PS_ERR_CUDA = -4,         /* a CUDA runtime call failed (see ps_last_cuda_error) */
+    PS_ERR_BUSY = -5,         /* server: admission budget or in-flight limit reached */
+    PS_ERR_TIMEOUT = -6,      /* a bounded wait expired */
+    PS_ERR_NOT_FOUND = -7     /* server: unknown request id */
+} ps_status;
+
+typedef enum {
+    PS_I32 = 0, PS_I64 = 1, PS_F32 = 2, PS_F64 = 3, PS_U32 = 4, PS_U64 = 5
+} ps_dtype;
+
+typedef enum {
+    PS_PIVOT_REGULAR = 0, /* PSRS: regular sampling (Sec. 2.3) */
+    PS_PIVOT_EXACT = 1    /* PSES: exact splitting (Sec. 2.3, Eq. 1, Eq. 2) */
+} ps_pivot_mode;
+
+/* Tuning parameters.  0 in a field means "choose automatically" (the
+ * library's size-binned default).  n_blocks = n_B and n_parts = n_P of
+ * Sec. 2; both may exceed n (empty blocks or partitions are legal).
+ * Limits: 1 <= n_blocks <= 4096, 1 <= n_parts <= 1048576. */
+typedef struct {
+    int64_t n_blocks;
+    int64_t n_parts;
+    int64_t reserved[2]; /* must be 0 */
+} ps_params;
+
+/* Optional record of the method's intermediates, for checking.  Each pointer
+ * may be NULL (that intermediate is not reported).  All are device pointers
+ * sized by the caller:
+ *   pivots         n_P-1 pivots P_1..P_{n_P-1} in the key's own dtype
+ *                  (for records: the uint64 key half)
+ *   pivot_payload  n_P-1 uint32 payload halves of the pivots (records only)
+ *   c              n_P-1 int64 tie counts c_k of Eq. 2 (exact splitting;
+ *                  zeros under regular sampling)
+ *   splits         n_B x (n_P+1) int64, row-major; splits[b*(n_P+1)+k] is the
+ *                  number of elements of sorted block b that lie in
+ *                  partitions 0..k-1
+ *   offsets        n_P+1 int64 partition offsets O_0 = 0 .. O_{n_P} = n
+ * The trace is written only when n >= 2. */
+typedef struct {
+    void* pivots;
+    uint32_t* pivot_payload;
+    int64_t* c;
+    int64_t* splits;
+    int64_t* offsets;
+} ps_trace;
+
+/* Sort n keys of `dtype` in place at `keys` (device memory, naturally
+ * aligned for the dtype), with automatic parameters.  n = 0 or 1 is a no-op.
+ * Returns PS_OK once all kernels are queued on `stream`. */
+int ps_sort(void* keys, int64_t n, int dtype, int pivot_mode, ps_stream_t stream);
+
+/* As ps_sort, with explicit parameters (NULL = automatic) and an optional
+ * trace (NULL = none). */
+int ps_sort_ex(void* keys, int64_t n, int dtype, int pivot_mode, const ps_params* params,
+               const ps_trace* trace, ps_stream_t stream);
+
+/* Sort n records in place, ordered by (key, payload): keys[i] and payload[i]
+ * form record i (structure of arrays, device memory). */
+int ps_sort_pairs(uint64_t* keys, uint32_t* payload, int64_t n, int pivot_mode,
+                  const ps_params* params, const ps_trace* trace, ps_stream_t stream);
+
+/* End-to-end form for callers whose keys live in HOST memory (pinned or
+ * pageable): copies the n keys to the device, sorts them as ps_sort_ex does,
+ * copies the result back into `host_keys`, and waits for `stream` to finish
+ * before returning.  Device buffers come from the library's pool. */
+int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode,
+                 const ps_params* params, ps_stream_t stream);
+
+/* The parameters a sort of n keys of `dtype` would use: copies `in` (or
+ * zeros when NULL) to `out` with every automatic field resolved. */
+int ps_resolve_params(int64_t n, int dtype, const ps_params* in, ps_params* out);
+
+/* Bytes of workspace one sort of n keys of `dtype` takes from the pool
+ * (dtype -1 = records). */
+int ps_workspace_bytes(int64_t n, int dtype, const ps_params* params, size_t* out);
+
+/* Static, human-readable text for a ps_status value. */
+const char* ps_status_string(int status);
+
+/* The cudaError_t of the last CUDA failure seen by this host thread (0 if
+ * none). */
+int ps_last_cuda_error(void);
+
+/* ---- profiling (library-wide, off by default) ---------------------------
+ * While enabled, every kernel the library launches is bracketed by two CUDA
+ * events recorded on the launch stream, so that per-kernel device time can be
+ * read back without an external profiler.  Recording adds two event records
+ * per launch; it does not synchronise. */
+typedef struct {
+    char name[32];     /* kernel label, e.g. "tile_sort", "merge_final" */
+    int64_t launches;  /* launches recorded since the last reset */
+    double total_ms;   /* summed device time of those launches */
+} ps_kernel_stat;
+
+/* Turn recording on (1) or off (0).  Returns the previous state. */
+int ps_profile_enable(int on);
+
+/* Wait for every recorded launch to finish, then write at most `cap`
+ * per-kernel aggregates to `out` and their count to *n (kernels in first-seen
+ * order).  Returns PS_ERR_CUDA if an event cannot be read. */
+int ps_profile_read(ps_kernel_stat* out, int cap, int* n);
+
+/* Forget all recorded launches. */
+int ps_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSORT_H */

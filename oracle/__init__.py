@@ -113,3 +113,37 @@ def sort(keys: np.ndarray, mode: int, n_blocks: int, n_parts: int,
         pivots = piv_bits[:npv].view(kd)
     return Result(out, out_pay, pivots.copy(), piv_pay[:npv].copy(), c[:npv].copy(),
                   splits, offsets)
+
+
+def order_key(keys: np.ndarray) -> np.ndarray:
+    """Order key of each key as an unsigned integer (numpy restatement of the
+    same reading as psort_oracle.c: sign flip for signed integers, IEEE
+    totalOrder bits for floats)."""
+    k = np.ascontiguousarray(keys)
+    if k.dtype == np.int32:
+        return k.view(np.uint32) ^ np.uint32(0x80000000)
+    if k.dtype == np.int64:
+        return k.view(np.uint64) ^ np.uint64(0x8000000000000000)
+    if k.dtype == np.float32:
+        u = k.view(np.uint32)
+        neg = (u >> np.uint32(31)).astype(bool)
+        return np.where(neg, ~u, u | np.uint32(0x80000000))
+    if k.dtype == np.float64:
+        u = k.view(np.uint64)
+        neg = (u >> np.uint64(63)).astype(bool)
+        return np.where(neg, ~u, u | np.uint64(0x8000000000000000))
+    if k.dtype in (np.uint32, np.uint64):
+        return k
+    raise TypeError(k.dtype)
+
+
+def reference_sort(keys: np.ndarray, payload: np.ndarray | None = None):
+    """The method's final result by its plain definition: the unique
+    permutation of the input that is ascending in (order key, payload).
+    numpy's stable argsort is the library step; used for inputs too large
+    for the step-by-step oracle."""
+    ok = order_key(keys)
+    if payload is None:
+        return keys[np.argsort(ok, kind="stable")]
+    idx = np.lexsort((np.asarray(payload, dtype=np.uint32), ok))
+    return keys[idx], np.asarray(payload)[idx]

@@ -1,0 +1,193 @@
+"""GB300-native parallel samplesort (Tokuue & Ishiyama, arXiv 2305.05245, Sec. 2).
+
+Thin Python binding over the C ABI of ``libpsort.so`` (include/psort.h).
+Every function here only marshals arguments: torch provides device memory
+and streams, and each step of the sort runs in the library's CUDA kernels.
+
+    import torch, paper_2305_05245_gb300 as ps
+    x = torch.randint(-2**31, 2**31, (1 << 20,), dtype=torch.int32, device="cuda")
+    ps.sort(x, "exact")            # in place, on the current stream
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+from . import _lib
+from ._lib import PS_PIVOT_EXACT, PS_PIVOT_REGULAR, PsortError  # noqa: F401
+
+__all__ = ["sort", "sort_pairs", "sort_host", "resolve_params", "workspace_bytes", "Trace",
+           "PsortError", "PS_PIVOT_EXACT", "PS_PIVOT_REGULAR", "profile_enable", "profile_read",
+           "profile_reset"]
+
+_MODES = {"regular": _lib.PS_PIVOT_REGULAR, "psrs": _lib.PS_PIVOT_REGULAR, 0: 0,
+          "exact": _lib.PS_PIVOT_EXACT, "pses": _lib.PS_PIVOT_EXACT, 1: 1}
+
+
+def _dtype_code(dt) -> int:
+    import torch
+    m = {torch.int32: _lib.PS_I32, torch.int64: _lib.PS_I64, torch.float32: _lib.PS_F32,
+         torch.float64: _lib.PS_F64}
+    if hasattr(torch, "uint32"):
+        m[torch.uint32] = _lib.PS_U32
+        m[torch.uint64] = _lib.PS_U64
+    if dt not in m:
+        raise TypeError("unsupported key dtype %s" % dt)
+    return m[dt]
+
+
+def _np_dtype_code(dt) -> int:
+    import numpy as np
+    m = {np.dtype(np.int32): _lib.PS_I32, np.dtype(np.int64): _lib.PS_I64,
+         np.dtype(np.float32): _lib.PS_F32, np.dtype(np.float64): _lib.PS_F64,
+         np.dtype(np.uint32): _lib.PS_U32, np.dtype(np.uint64): _lib.PS_U64}
+    return m[np.dtype(dt)]
+
+
+def _mode(m) -> int:
+    try:
+        return _MODES[m]
+    except KeyError:
+        raise ValueError("pivot mode must be 'regular' or 'exact'") from None
+
+
+def _params(n_blocks: int, n_parts: int):
+    p = _lib.PsParams()
+    p.n_blocks = n_blocks
+    p.n_parts = n_parts
+    return p
+
+
+def _stream_handle(stream) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+@dataclass
+class Trace:
+    """Intermediates of one sort (device tensors): pivots P_1..P_{n_P-1},
+    pivot payloads (records), tie counts c_k (Eq. 2), the n_B x (n_P+1) split
+    table, and the partition offsets O_0..O_{n_P}."""
+    pivots: object
+    pivot_payload: object
+    c: object
+    splits: object
+    offsets: object
+    n_blocks: int
+    n_parts: int
+
+
+def resolve_params(n: int, dtype_code: int, n_blocks: int = 0, n_parts: int = 0) -> tuple[int, int]:
+    """(n_B, n_P) that a sort of n keys would use (0 = automatic)."""
+    lib = _lib.load()
+    out = _lib.PsParams()
+    _lib.check(lib, "ps_resolve_params",
+               lib.ps_resolve_params(n, dtype_code, ctypes.byref(_params(n_blocks, n_parts)),
+                                     ctypes.byref(out)))
+    return out.n_blocks, out.n_parts
+
+
+def workspace_bytes(n: int, dtype_code: int, n_blocks: int = 0, n_parts: int = 0) -> int:
+    lib = _lib.load()
+    out = ctypes.c_size_t()
+    _lib.check(lib, "ps_workspace_bytes",
+               lib.ps_workspace_bytes(n, dtype_code, ctypes.byref(_params(n_blocks, n_parts)),
+                                      ctypes.byref(out)))
+    return out.value
+
+
+def _make_trace(n: int, code: int, n_blocks: int, n_parts: int, key_dtype, device, records: bool):
+    import torch
+    nb, npart = resolve_params(n, -1 if records else code, n_blocks, n_parts)
+    t = Trace(pivots=torch.zeros(max(npart - 1, 1), dtype=key_dtype, device=device),
+              pivot_payload=torch.zeros(max(npart - 1, 1), dtype=torch.int32, device=device),
+              c=torch.zeros(max(npart - 1, 1), dtype=torch.int64, device=device),
+              splits=torch.zeros((nb, npart + 1), dtype=torch.int64, device=device),
+              offsets=torch.zeros(npart + 1, dtype=torch.int64, device=device),
+              n_blocks=nb, n_parts=npart)
+    ct = _lib.PsTrace()
+    ct.pivots = t.pivots.data_ptr()
+    ct.pivot_payload = t.pivot_payload.data_ptr() if records else None
+    ct.c = t.c.data_ptr()
+    ct.splits = t.splits.data_ptr()
+    ct.offsets = t.offsets.data_ptr()
+    return t, ct
+
+
+def sort(keys, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, trace: bool = False,
+         stream=None):
+    """Sort a contiguous 1-D CUDA tensor in place (int32, int64, float32,
+    float64, uint32, uint64).  Returns a Trace when ``trace`` is true."""
+    lib = _lib.load()
+    if not keys.is_cuda or keys.dim() != 1 or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous 1-D CUDA tensor")
+    code = _dtype_code(keys.dtype)
+    n = keys.numel()
+    tr, ct = (None, None)
+    if trace:
+        tr, ct = _make_trace(n, code, n_blocks, n_parts, keys.dtype, keys.device, False)
+    rc = lib.ps_sort_ex(keys.data_ptr() if n else None, n, code, _mode(pivot_mode),
+                        ctypes.byref(_params(n_blocks, n_parts)),
+                        ctypes.byref(ct) if ct is not None else None, _stream_handle(stream))
+    _lib.check(lib, "ps_sort_ex", rc)
+    return tr
+
+
+def sort_pairs(keys, payload, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0,
+               trace: bool = False, stream=None):
+    """Sort records in place by (key, payload): ``keys`` a contiguous 1-D CUDA
+    tensor of 64-bit keys (int64 storage read as unsigned), ``payload`` one of
+    32-bit payloads (int32 storage read as unsigned)."""
+    lib = _lib.load()
+    n = keys.numel()
+    if payload.numel() != n or keys.element_size() != 8 or payload.element_size() != 4:
+        raise ValueError("records need 64-bit keys and 32-bit payloads of equal length")
+    if not (keys.is_cuda and payload.is_cuda and keys.is_contiguous() and payload.is_contiguous()):
+        raise ValueError("keys and payload must be contiguous CUDA tensors")
+    tr, ct = (None, None)
+    if trace:
+        tr, ct = _make_trace(n, -1, n_blocks, n_parts, keys.dtype, keys.device, True)
+    rc = lib.ps_sort_pairs(keys.data_ptr() if n else None, payload.data_ptr() if n else None, n,
+                           _mode(pivot_mode), ctypes.byref(_params(n_blocks, n_parts)),
+                           ctypes.byref(ct) if ct is not None else None, _stream_handle(stream))
+    _lib.check(lib, "ps_sort_pairs", rc)
+    return tr
+
+
+def sort_host(arr, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, stream=None) -> None:
+    """Sort a host array in place through ps_sort_host (copies to the device,
+    sorts, copies back, waits).  ``arr`` is a contiguous numpy array or a CPU
+    torch tensor (pinned memory gives the fastest copies)."""
+    lib = _lib.load()
+    import numpy as np
+    if isinstance(arr, np.ndarray):
+        if not arr.flags["C_CONTIGUOUS"]:
+            raise ValueError("host array must be contiguous")
+        code, ptr, n = _np_dtype_code(arr.dtype), arr.ctypes.data, arr.size
+    else:
+        if arr.is_cuda or not arr.is_contiguous():
+            raise ValueError("host tensor must be a contiguous CPU tensor")
+        code, ptr, n = _dtype_code(arr.dtype), arr.data_ptr(), arr.numel()
+    rc = lib.ps_sort_host(ptr if n else None, n, code, _mode(pivot_mode),
+                          ctypes.byref(_params(n_blocks, n_parts)), _stream_handle(stream))
+    _lib.check(lib, "ps_sort_host", rc)
+
+
+def profile_enable(on: bool = True) -> bool:
+    """Record per-kernel CUDA events around every library launch."""
+    return bool(_lib.load().ps_profile_enable(1 if on else 0))
+
+
+def profile_reset() -> None:
+    _lib.check(_lib.load(), "ps_profile_reset", _lib.load().ps_profile_reset())
+
+
+def profile_read() -> dict:
+    """{kernel label: (launches, total device ms)} since the last reset."""
+    lib = _lib.load()
+    cap = 64
+    buf = (_lib.PsKernelStat * cap)()
+    n = ctypes.c_int()
+    _lib.check(lib, "ps_profile_read", lib.ps_profile_read(buf, cap, ctypes.byref(n)))
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n.value, cap))}

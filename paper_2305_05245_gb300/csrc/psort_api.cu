@@ -1,0 +1,328 @@
+// psort_api.cu -- the C ABI declared in include/psort.h: argument checks,
+// automatic parameters, the workspace pool, and dispatch to the key families.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "psort_internal.h"
+
+namespace ps {
+
+static thread_local int g_last_cuda = 0;
+
+int fail_cuda(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    if (e == cudaErrorMemoryAllocation) return PS_ERR_NO_MEMORY;
+    return PS_ERR_CUDA;
+}
+
+// One stream-ordered memory pool per device, created on first use and kept
+// for the life of the process; freed blocks stay cached in the pool.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static int get_pool(cudaMemPool_t* out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (dev < 0 || dev >= 64) return PS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return fail_cuda(e);
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return fail_cuda(e);
+        g_pool[dev] = p;
+    }
+    *out = g_pool[dev];
+    return PS_OK;
+}
+
+int ws_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    cudaMemPool_t pool;
+    int rc = get_pool(&pool);
+    if (rc != PS_OK) return rc;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 256, pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail_cuda(e);
+    }
+    return PS_OK;
+}
+
+void ws_free(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ---- profiling records
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mu;
+static std::vector<ProfRec> g_prof_recs;
+
+bool prof_on() { return g_prof.load(std::memory_order_relaxed); }
+
+int prof_begin(const char* name, cudaStream_t s)
+{
+    ProfRec r;
+    r.name = name;
+    if (cudaEventCreate(&r.a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&r.b) != cudaSuccess) {
+        cudaEventDestroy(r.a);
+        return -1;
+    }
+    cudaEventRecord(r.a, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_recs.push_back(r);
+    return (int)g_prof_recs.size() - 1;
+}
+
+void prof_end(int rec, cudaStream_t s)
+{
+    cudaEvent_t b;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (rec < 0 || rec >= (int)g_prof_recs.size()) return;
+        b = g_prof_recs[rec].b;
+    }
+    cudaEventRecord(b, s);
+}
+
+static void prof_clear()
+{
+    for (auto& r : g_prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof_recs.clear();
+}
+
+static const int64_t MAX_BLOCKS = 4096;
+static const int64_t MAX_PARTS = 1 << 20;
+
+static int64_t pow2_floor(int64_t x)
+{
+    int64_t p = 1;
+    while (p * 2 <= x) p *= 2;
+    return p;
+}
+
+// Size-binned defaults: blocks of about 2^19 keys (2^18 for records), at
+// most 1024 blocks; partitions of about 2^17 keys.
+static void resolve(int64_t n, int dtype, const ps_params* in, ps_params* out)
+{
+    ps_params r;
+    memset(&r, 0, sizeof(r));
+    if (in) r = *in;
+    const int64_t blk = dtype < 0 ? (1 << 18) : (1 << 19);
+    if (r.n_blocks <= 0) r.n_blocks = std::min<int64_t>(1024, std::max<int64_t>(1, pow2_floor(n / blk)));
+    if (r.n_parts <= 0) r.n_parts = std::min<int64_t>(4096, std::max<int64_t>(1, pow2_floor(n / (1 << 17))));
+    *out = r;
+}
+
+static int check_params(const ps_params* p)
+{
+    if (!p) return PS_OK;
+    if (p->n_blocks < 0 || p->n_blocks > MAX_BLOCKS) return PS_ERR_INVALID_ARG;
+    if (p->n_parts < 0 || p->n_parts > MAX_PARTS) return PS_ERR_INVALID_ARG;
+    if (p->reserved[0] != 0 || p->reserved[1] != 0) return PS_ERR_INVALID_ARG;
+    return PS_OK;
+}
+
+static int dispatch(SortArgs& a)
+{
+    switch (a.dtype) {
+    case PS_I32: case PS_F32: case PS_U32: return run_sort_u32(a);
+    case PS_I64: case PS_F64: case PS_U64: return run_sort_u64(a);
+    case -1: return run_sort_rec(a);
+    default: return PS_ERR_UNSUPPORTED;
+    }
+}
+
+static int sort_common(void* keys, uint32_t* payload, int64_t n, int dtype, int mode, const ps_params* params,
+                       const ps_trace* trace, ps_stream_t stream)
+{
+    if (n < 0) return PS_ERR_INVALID_ARG;
+    if (dtype < -1 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
+    if (mode != PS_PIVOT_REGULAR && mode != PS_PIVOT_EXACT) return PS_ERR_UNSUPPORTED;
+    int rc = check_params(params);
+    if (rc != PS_OK) return rc;
+    if (n <= 1) return PS_OK;
+    if (!keys || (dtype == -1 && !payload)) return PS_ERR_INVALID_ARG;
+    const size_t align = (dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32) ? 4 : 8;
+    if ((uintptr_t)keys % align != 0 || (payload && (uintptr_t)payload % 4 != 0)) return PS_ERR_INVALID_ARG;
+    ps_params r;
+    resolve(n, dtype, params, &r);
+    SortArgs a;
+    a.keys = keys;
+    a.payload = payload;
+    a.n = n;
+    a.dtype = dtype;
+    a.mode = mode;
+    a.n_B = r.n_blocks;
+    a.n_P = r.n_parts;
+    a.trace = trace;
+    a.stream = (cudaStream_t)stream;
+    return dispatch(a);
+}
+
+static size_t dtype_size(int dtype)
+{
+    return (dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32) ? 4 : 8;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" {
+
+int ps_sort(void* keys, int64_t n, int dtype, int pivot_mode, ps_stream_t stream)
+{
+    if (dtype < 0) return PS_ERR_UNSUPPORTED;
+    return sort_common(keys, nullptr, n, dtype, pivot_mode, nullptr, nullptr, stream);
+}
+
+int ps_sort_ex(void* keys, int64_t n, int dtype, int pivot_mode, const ps_params* params, const ps_trace* trace,
+               ps_stream_t stream)
+{
+    if (dtype < 0) return PS_ERR_UNSUPPORTED;
+    return sort_common(keys, nullptr, n, dtype, pivot_mode, params, trace, stream);
+}
+
+int ps_sort_pairs(uint64_t* keys, uint32_t* payload, int64_t n, int pivot_mode, const ps_params* params,
+                  const ps_trace* trace, ps_stream_t stream)
+{
+    return sort_common(keys, payload, n, -1, pivot_mode, params, trace, stream);
+}
+
+int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode, const ps_params* params, ps_stream_t stream)
+{
+    if (dtype < 0 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
+    if (pivot_mode != PS_PIVOT_REGULAR && pivot_mode != PS_PIVOT_EXACT) return PS_ERR_UNSUPPORTED;
+    if (n < 0) return PS_ERR_INVALID_ARG;
+    int rc = check_params(params);
+    if (rc != PS_OK) return rc;
+    if (n <= 1) return PS_OK;
+    if (!host_keys) return PS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * dtype_size(dtype);
+    void* d = nullptr;
+    rc = ws_alloc(&d, bytes, s);
+    if (rc != PS_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(d, host_keys, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        rc = sort_common(d, nullptr, n, dtype, pivot_mode, params, nullptr, stream);
+        if (rc == PS_OK) e = cudaMemcpyAsync(host_keys, d, bytes, cudaMemcpyDeviceToHost, s);
+    }
+    ws_free(d, s);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (rc != PS_OK) return rc;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return PS_OK;
+}
+
+int ps_resolve_params(int64_t n, int dtype, const ps_params* in, ps_params* out)
+{
+    if (!out || n < 0) return PS_ERR_INVALID_ARG;
+    if (dtype < -1 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
+    int rc = check_params(in);
+    if (rc != PS_OK) return rc;
+    resolve(n, dtype, in, out);
+    return PS_OK;
+}
+
+int ps_workspace_bytes(int64_t n, int dtype, const ps_params* params, size_t* out)
+{
+    if (!out || n < 0) return PS_ERR_INVALID_ARG;
+    if (dtype < -1 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
+    int rc = check_params(params);
+    if (rc != PS_OK) return rc;
+    if (n <= 1) {
+        *out = 0;
+        return PS_OK;
+    }
+    ps_params r;
+    resolve(n, dtype, params, &r);
+    switch (dtype) {
+    case PS_I32: case PS_F32: case PS_U32: *out = ws_bytes_u32(n, r.n_blocks, r.n_parts); break;
+    case -1: *out = ws_bytes_rec(n, r.n_blocks, r.n_parts); break;
+    default: *out = ws_bytes_u64(n, r.n_blocks, r.n_parts); break;
+    }
+    return PS_OK;
+}
+
+const char* ps_status_string(int status)
+{
+    switch (status) {
+    case PS_OK: return "ok";
+    case PS_ERR_INVALID_ARG: return "invalid argument";
+    case PS_ERR_UNSUPPORTED: return "unsupported dtype or pivot mode";
+    case PS_ERR_NO_MEMORY: return "out of device memory";
+    case PS_ERR_CUDA: return "CUDA runtime error";
+    case PS_ERR_BUSY: return "busy: admission budget or in-flight limit reached";
+    case PS_ERR_TIMEOUT: return "timed out";
+    case PS_ERR_NOT_FOUND: return "unknown request id";
+    default: return "unknown status";
+    }
+}
+
+int ps_last_cuda_error(void) { return g_last_cuda; }
+
+int ps_profile_enable(int on) { return g_prof.exchange(on != 0) ? 1 : 0; }
+
+int ps_profile_read(ps_kernel_stat* out, int cap, int* n)
+{
+    if (!n || cap < 0 || (cap > 0 && !out)) return PS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<ps_kernel_stat> agg;
+    for (auto& r : g_prof_recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return fail_cuda(e);
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return fail_cuda(e);
+        size_t i = 0;
+        for (; i < agg.size(); i++)
+            if (r.name == agg[i].name) break;
+        if (i == agg.size()) {
+            ps_kernel_stat st;
+            memset(&st, 0, sizeof(st));
+            strncpy(st.name, r.name.c_str(), sizeof(st.name) - 1);
+            agg.push_back(st);
+        }
+        agg[i].launches++;
+        agg[i].total_ms += ms;
+    }
+    int k = 0;
+    for (; k < (int)agg.size() && k < cap; k++) out[k] = agg[k];
+    *n = (int)agg.size();
+    return PS_OK;
+}
+
+int ps_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_clear();
+    return PS_OK;
+}
+
+}  // extern "C"

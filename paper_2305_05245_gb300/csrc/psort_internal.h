@@ -1,0 +1,53 @@
+// psort_internal.h -- host-side declarations shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/psort.h"
+
+namespace ps {
+
+// One sort request after argument validation and parameter resolution.
+struct SortArgs {
+    void* keys;          // device keys (records: uint64 keys)
+    uint32_t* payload;   // records only
+    int64_t n;
+    int dtype;           // ps_dtype, or -1 for records
+    int mode;            // ps_pivot_mode
+    int64_t n_B, n_P;    // resolved
+    const ps_trace* trace;
+    cudaStream_t stream;
+};
+
+// Workspace from the library's stream-ordered pool.
+int ws_alloc(void** p, size_t bytes, cudaStream_t s);
+void ws_free(void* p, cudaStream_t s);
+int fail_cuda(cudaError_t e);
+
+// Profiling: when enabled (ps_profile_enable), a ProfScope records a CUDA
+// event before and after the launch it brackets.
+bool prof_on();
+int prof_begin(const char* name, cudaStream_t s);  // returns a record index or -1
+void prof_end(int rec, cudaStream_t s);
+struct ProfScope {
+    int rec;
+    cudaStream_t s;
+    ProfScope(const char* name, cudaStream_t st) : rec(prof_on() ? prof_begin(name, st) : -1), s(st) {}
+    ~ProfScope()
+    {
+        if (rec >= 0) prof_end(rec, s);
+    }
+};
+
+// Per key family (defined in psort_u32.cu, psort_u64.cu, psort_rec.cu).
+int run_sort_u32(const SortArgs& a);
+int run_sort_u64(const SortArgs& a);
+int run_sort_rec(const SortArgs& a);
+size_t ws_bytes_u32(int64_t n, int64_t n_B, int64_t n_P);
+size_t ws_bytes_u64(int64_t n, int64_t n_B, int64_t n_P);
+size_t ws_bytes_rec(int64_t n, int64_t n_B, int64_t n_P);
+
+}  // namespace ps

@@ -1,0 +1,856 @@
+// psort_kernels.cuh -- device code of the GB300 parallel samplesort.
+//
+// Four steps of Tokuue & Ishiyama (arXiv 2305.05245), Sec. 2, mapped to
+// kernels:
+//   step 1 (sort each block)   k_tile_sort: tiles of NT*E keys sorted in shared
+//                              memory (register sorting network + merge-path
+//                              levels); blocks longer than a tile are finished
+//                              by in-block multiway merge passes (merge job 0).
+//   step 2 (pivots)            k_psrs_samples + k_psrs_select (regular
+//                              sampling, Sec. 2.3) or k_pses (exact splitting,
+//                              Eq. 1 and Eq. 2, value bisection with per-block
+//                              binary-search counts as Sec. 2.3 describes).
+//   step 3 (partitioning)      k_psrs_splits / k_pses (split table), then
+//                              k_offsets (O_k = sum_b s[b][k], Sec. 2).
+//   step 4 (multiway merge)    merge job 1: each partition's pieces are cut
+//                              into chunks at splitters taken from a sorted
+//                              sample pool (k_pool, k_corank) and every chunk
+//                              is merged in shared memory (k_merge).
+// Keys travel as order keys kappa (unsigned integers whose order is the sort
+// order); the transform is fused into the first load and the last store.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ps {
+
+// ---------------------------------------------------------------- key types
+
+// A record: 64-bit key and 32-bit payload, ordered by (key, payload).
+struct Rec {
+    uint64_t k;
+    uint32_t p;
+};
+
+__device__ __forceinline__ bool key_lt(uint32_t a, uint32_t b) { return a < b; }
+__device__ __forceinline__ bool key_lt(uint64_t a, uint64_t b) { return a < b; }
+__device__ __forceinline__ bool key_lt(const Rec& a, const Rec& b)
+{
+    return a.k < b.k || (a.k == b.k && a.p < b.p);
+}
+
+// Traits: the value domain of each key type as an unsigned integer U, used
+// by the value bisection of exact splitting.
+template <typename K> struct KT;
+template <> struct KT<uint32_t> {
+    using U = uint32_t;
+    __device__ static U to_u(uint32_t k) { return k; }
+    __device__ static uint32_t from_u(U u) { return u; }
+    __device__ static U umax() { return 0xFFFFFFFFu; }
+    __device__ static uint32_t maxkey() { return 0xFFFFFFFFu; }
+};
+template <> struct KT<uint64_t> {
+    using U = uint64_t;
+    __device__ static U to_u(uint64_t k) { return k; }
+    __device__ static uint64_t from_u(U u) { return u; }
+    __device__ static U umax() { return ~0ull; }
+    __device__ static uint64_t maxkey() { return ~0ull; }
+};
+template <> struct KT<Rec> {
+    using U = unsigned __int128;
+    __device__ static U to_u(const Rec& r) { return ((U)r.k << 32) | (U)r.p; }
+    __device__ static Rec from_u(U u) { return Rec{(uint64_t)(u >> 32), (uint32_t)u}; }
+    __device__ static U umax() { return (((U)1) << 96) - 1; }
+    __device__ static Rec maxkey() { return Rec{~0ull, 0xFFFFFFFFu}; }
+};
+
+// ------------------------------------------------------- order-key transform
+// XF = 0: unsigned (identity), 1: two's complement (flip the sign bit),
+// 2: IEEE float (totalOrder: negative values inverted, others get the sign bit).
+template <int XF> __device__ __forceinline__ uint32_t kappa(uint32_t x)
+{
+    if (XF == 1) return x ^ 0x80000000u;
+    if (XF == 2) return (x & 0x80000000u) ? ~x : (x | 0x80000000u);
+    return x;
+}
+template <int XF> __device__ __forceinline__ uint32_t kappa_inv(uint32_t k)
+{
+    if (XF == 1) return k ^ 0x80000000u;
+    if (XF == 2) return (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    return k;
+}
+template <int XF> __device__ __forceinline__ uint64_t kappa(uint64_t x)
+{
+    if (XF == 1) return x ^ 0x8000000000000000ull;
+    if (XF == 2) return (x & 0x8000000000000000ull) ? ~x : (x | 0x8000000000000000ull);
+    return x;
+}
+template <int XF> __device__ __forceinline__ uint64_t kappa_inv(uint64_t k)
+{
+    if (XF == 1) return k ^ 0x8000000000000000ull;
+    if (XF == 2) return (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    return k;
+}
+
+// ------------------------------------------------------------ global buffers
+template <typename K> struct GBuf;
+template <> struct GBuf<uint32_t> {
+    uint32_t* p;
+    __device__ uint32_t ld(int64_t i) const { return p[i]; }
+    __device__ void st(int64_t i, uint32_t v) const { p[i] = v; }
+    template <int XF> __device__ uint32_t ldx(int64_t i) const { return kappa<XF>(p[i]); }
+    template <int XF> __device__ void stx(int64_t i, uint32_t v) const { p[i] = kappa_inv<XF>(v); }
+};
+template <> struct GBuf<uint64_t> {
+    uint64_t* p;
+    __device__ uint64_t ld(int64_t i) const { return p[i]; }
+    __device__ void st(int64_t i, uint64_t v) const { p[i] = v; }
+    template <int XF> __device__ uint64_t ldx(int64_t i) const { return kappa<XF>(p[i]); }
+    template <int XF> __device__ void stx(int64_t i, uint64_t v) const { p[i] = kappa_inv<XF>(v); }
+};
+template <> struct GBuf<Rec> {
+    uint64_t* k;
+    uint32_t* p;
+    __device__ Rec ld(int64_t i) const { return Rec{k[i], p[i]}; }
+    __device__ void st(int64_t i, const Rec& v) const { k[i] = v.k; p[i] = v.p; }
+    template <int XF> __device__ Rec ldx(int64_t i) const { return Rec{k[i], p[i]}; }
+    template <int XF> __device__ void stx(int64_t i, const Rec& v) const { k[i] = v.k; p[i] = v.p; }
+};
+
+// ---------------------------------------------- shared-memory buffers (padded)
+// One pad slot after every 128 bytes, so that thread t reading its E
+// consecutive elements (blocked layout) hits distinct banks.
+template <typename K> struct SBuf;
+template <> struct SBuf<uint32_t> {
+    uint32_t* a;
+    __device__ __forceinline__ uint32_t ld(int i) const { return a[i + (i >> 5)]; }
+    __device__ __forceinline__ void st(int i, uint32_t v) const { a[i + (i >> 5)] = v; }
+    static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / 32 + 1) * 4 + 15) & ~(size_t)15; }
+    static __device__ SBuf carve(char*& sp, int n) { SBuf b{(uint32_t*)sp}; sp += bytes(n); return b; }
+};
+template <> struct SBuf<uint64_t> {
+    uint64_t* a;
+    __device__ __forceinline__ uint64_t ld(int i) const { return a[i + (i >> 4)]; }
+    __device__ __forceinline__ void st(int i, uint64_t v) const { a[i + (i >> 4)] = v; }
+    static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / 16 + 1) * 8 + 15) & ~(size_t)15; }
+    static __device__ SBuf carve(char*& sp, int n) { SBuf b{(uint64_t*)sp}; sp += bytes(n); return b; }
+};
+template <> struct SBuf<Rec> {
+    SBuf<uint64_t> k;
+    SBuf<uint32_t> p;
+    __device__ __forceinline__ Rec ld(int i) const { return Rec{k.ld(i), p.ld(i)}; }
+    __device__ __forceinline__ void st(int i, const Rec& v) const { k.st(i, v.k); p.st(i, v.p); }
+    static __host__ __device__ size_t bytes(int n) { return SBuf<uint64_t>::bytes(n) + SBuf<uint32_t>::bytes(n); }
+    static __device__ SBuf carve(char*& sp, int n)
+    {
+        SBuf b;
+        b.k = SBuf<uint64_t>::carve(sp, n);
+        b.p = SBuf<uint32_t>::carve(sp, n);
+        return b;
+    }
+};
+
+// Storage views used by the merge routine: plain keys, or keys carrying a
+// 64-bit tag (run index and position of a pool sample).  Comparison is on
+// the key only; the merge is stable, so ties keep piece order.
+template <typename K> struct SKeys {
+    using V = K;
+    SBuf<K> b;
+    __device__ __forceinline__ V ld(int i) const { return b.ld(i); }
+    __device__ __forceinline__ void st(int i, const V& v) const { b.st(i, v); }
+    __device__ __forceinline__ static bool lt(const V& x, const V& y) { return key_lt(x, y); }
+};
+template <typename K> struct Tagged {
+    K key;
+    uint64_t tag;
+};
+template <typename K> struct STagged {
+    using V = Tagged<K>;
+    SBuf<K> kb;
+    SBuf<uint64_t> tb;
+    __device__ __forceinline__ V ld(int i) const { return V{kb.ld(i), tb.ld(i)}; }
+    __device__ __forceinline__ void st(int i, const V& v) const { kb.st(i, v.key); tb.st(i, v.tag); }
+    __device__ __forceinline__ static bool lt(const V& x, const V& y) { return key_lt(x.key, y.key); }
+    static __host__ __device__ size_t bytes(int n) { return SBuf<K>::bytes(n) + SBuf<uint64_t>::bytes(n); }
+};
+
+// ------------------------------------------------------- block-wide helpers
+template <int NT> __device__ int64_t block_sum(int64_t v)
+{
+    __shared__ int64_t red[NT / 32];
+    __shared__ int64_t total;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int64_t w = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, o);
+        if (threadIdx.x == 0) total = w;
+    }
+    __syncthreads();
+    int64_t t = total;
+    __syncthreads();
+    return t;
+}
+
+// Exclusive scan of one int64 per thread in thread order; returns this
+// thread's exclusive prefix and writes the block total to *tot.
+template <int NT> __device__ int64_t block_exscan(int64_t v, int64_t* tot)
+{
+    __shared__ int64_t wsum[NT / 32];
+    __shared__ int64_t total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < NT / 32 ? wsum[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < NT / 32) wsum[lane] = wi - w;
+        if (lane == 31) total = wi;
+    }
+    __syncthreads();
+    int64_t r = wsum[warp] + x - v;
+    *tot = total;
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------- register sorting network
+// Batcher's odd-even merge sort (Knuth, TAOCP vol. 3, 5.3.4) on E register
+// values, E a power of two; every index is a compile-time constant.
+template <typename K> __device__ __forceinline__ void cas(K& a, K& b)
+{
+    bool s = key_lt(b, a);
+    K lo = s ? b : a;
+    K hi = s ? a : b;
+    a = lo;
+    b = hi;
+}
+// Odd-even merge of the N elements starting at LO taken with stride R: merge
+// the even and the odd subsequences recursively, then compare neighbours.
+template <int LO, int N, int R> struct OddEvenMerge {
+    template <typename K, int E> __device__ __forceinline__ static void run(K (&a)[E])
+    {
+        constexpr int M = R * 2;
+        if constexpr (M < N) {
+            OddEvenMerge<LO, N, M>::run(a);
+            OddEvenMerge<LO + R, N, M>::run(a);
+#pragma unroll
+            for (int i = LO + R; i + R < LO + N; i += M) cas(a[i], a[i + R]);
+        } else {
+            cas(a[LO], a[LO + R]);
+        }
+    }
+};
+template <int LO, int N> struct OddEvenSort {
+    template <typename K, int E> __device__ __forceinline__ static void run(K (&a)[E])
+    {
+        if constexpr (N > 1) {
+            OddEvenSort<LO, N / 2>::run(a);
+            OddEvenSort<LO + N / 2, N / 2>::run(a);
+            OddEvenMerge<LO, N, 1>::run(a);
+        }
+    }
+};
+template <int E, typename K> __device__ __forceinline__ void reg_sort(K (&r)[E])
+{
+    static_assert((E & (E - 1)) == 0, "E must be a power of two");
+    OddEvenSort<0, E>::run(r);
+}
+
+// -------------------------------------------- shared-memory multiway merge
+// The n elements of `s` form P sorted pieces with boundaries off[0..P]
+// (off[0] = 0, off[P] = n, in shared memory).  Pairs of adjacent units are
+// merged level by level (merge path: each thread finds where its E outputs
+// start by binary search, then merges them serially); after ceil(log2 P)
+// levels the n elements are one sorted run, in place.  Ties keep the lower
+// piece first.  Requires n <= NT*E.  Called by all threads of the block.
+template <int NT, int E, typename S>
+__device__ void merge_pieces(const S& s, const int* off, int P, int n)
+{
+    using V = typename S::V;
+    const int pos0 = threadIdx.x * E;
+    const int cnt = n - pos0 < E ? n - pos0 : E;
+    for (int w = 1; w < P; w <<= 1) {
+        V out[E];
+        if (cnt > 0) {
+            const int nunits = (P + 2 * w - 1) / (2 * w);
+            // the unit holding output position pos0: the last unit starting at or before it
+            int lo = 0, hi = nunits - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                int st = off[min(mid * 2 * w, P)];
+                if (st <= pos0) lo = mid;
+                else hi = mid - 1;
+            }
+            int u = lo;
+            int us = off[min(u * 2 * w, P)], um = off[min(u * 2 * w + w, P)], ue = off[min(u * 2 * w + 2 * w, P)];
+            // merge path inside unit u: how many of the first d outputs come from A
+            const int d = pos0 - us, alen = um - us, blen = ue - um;
+            int a0 = d - blen > 0 ? d - blen : 0, a1 = d < alen ? d : alen;
+            while (a0 < a1) {
+                int mid = (a0 + a1) >> 1;
+                if (!S::lt(s.ld(um + d - 1 - mid), s.ld(us + mid))) a0 = mid + 1;
+                else a1 = mid;
+            }
+            int ai = us + a0, bi = um + d - a0;
+            V av = s.ld(ai < um ? ai : us);
+            V bv = s.ld(bi < ue ? bi : um);
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                if (i < cnt) {
+                    if (ai >= um && bi >= ue) {
+                        // this unit is exhausted: continue with the next non-empty unit
+                        do {
+                            u++;
+                            us = ue;
+                            um = off[min(u * 2 * w + w, P)];
+                            ue = off[min(u * 2 * w + 2 * w, P)];
+                        } while (us == ue && u < nunits);
+                        ai = us;
+                        bi = um;
+                        av = s.ld(ai < um ? ai : us);
+                        bv = s.ld(bi < ue ? bi : um);
+                    }
+                    bool ta = ai < um && (bi >= ue || !S::lt(bv, av));
+                    out[i] = ta ? av : bv;
+                    if (ta) {
+                        ai++;
+                        if (ai < um) av = s.ld(ai);
+                    } else {
+                        bi++;
+                        if (bi < ue) bv = s.ld(bi);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (cnt > 0) {
+#pragma unroll
+            for (int i = 0; i < E; i++)
+                if (i < cnt) s.st(pos0 + i, out[i]);
+        }
+        __syncthreads();
+    }
+}
+
+// Number of elements of the sorted range src[lo, hi) that are < v (lower
+// bound, STRICT = true) or <= v (upper bound, STRICT = false).
+template <bool STRICT, typename K>
+__device__ __forceinline__ int64_t bound(const GBuf<K>& src, int64_t lo, int64_t hi, const K& v)
+{
+    int64_t a = lo, b = hi;
+    while (a < b) {
+        int64_t m = a + ((b - a) >> 1);
+        K x = src.ld(m);
+        bool go_right = STRICT ? key_lt(x, v) : !key_lt(v, x);
+        if (go_right) a = m + 1;
+        else b = m;
+    }
+    return a - lo;
+}
+
+// ------------------------------------------------------------ step 1: tiles
+// One CTA sorts one tile of NT*E keys of one block (tiles never straddle a
+// block boundary).  Loads apply the order-key transform XF.  The tile is
+// padded with the largest key, which sorts last and is never written.
+template <int NT, int E, typename K, int XF>
+__global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, int64_t N, int64_t L,
+                                                  int64_t tiles_per_block)
+{
+    constexpr int T = NT * E;
+    extern __shared__ __align__(16) char smem[];
+    char* sp = smem;
+    SBuf<K> sb = SBuf<K>::carve(sp, T);
+    int* off = (int*)sp;
+    const int64_t b = blockIdx.x / tiles_per_block, t = blockIdx.x - b * tiles_per_block;
+    const int64_t bs = b * L < N ? b * L : N;
+    const int64_t be = bs + L < N ? bs + L : N;
+    const int64_t ts = bs + t * T;
+    if (ts >= be) return;
+    const int n = (int)(be - ts < T ? be - ts : T);
+    for (int i = threadIdx.x; i < T; i += NT) sb.st(i, i < n ? src.template ldx<XF>(ts + i) : KT<K>::maxkey());
+    for (int i = threadIdx.x; i <= NT; i += NT) off[i] = i * E;
+    __syncthreads();
+    K r[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) r[j] = sb.ld(threadIdx.x * E + j);
+    reg_sort<E>(r);
+#pragma unroll
+    for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
+    __syncthreads();
+    merge_pieces<NT, E>(SKeys<K>{sb}, off, NT, T);
+    for (int i = threadIdx.x; i < n; i += NT) dst.st(ts + i, sb.ld(i));
+}
+
+// ----------------------------------------------------------- merge jobs
+// A merge job is a set of groups; group g merges K sorted runs of `src`
+// into one sorted range of `dst` starting at out_base(g).
+//   kind 0 (in-block pass, step 1): group = (block b, index gi); run r covers
+//          [bs + (gi*K + r)*W, +W) clipped to the block; output in place.
+//   kind 1 (final merge, step 4): group = partition k; run r = block r's
+//          piece [bs + s[r][k], bs + s[r][k+1]); output at O_k.
+struct MergeJob {
+    int kind;
+    int K;
+    int64_t N, L;
+    int64_t W, gpb;                  // kind 0
+    const int64_t* splits;           // kind 1
+    const int64_t* offsets;          // kind 1
+    int64_t n_P;                     // kind 1
+    __device__ __forceinline__ void run(int64_t g, int r, int64_t& lo, int64_t& hi) const
+    {
+        if (kind == 0) {
+            int64_t b = g / gpb, gi = g - b * gpb;
+            int64_t bs = b * L < N ? b * L : N;
+            int64_t be = bs + L < N ? bs + L : N;
+            int64_t s = bs + (gi * K + r) * W;
+            lo = s < be ? s : be;
+            hi = s + W < be ? s + W : be;
+        } else {
+            int64_t bs = (int64_t)r * L < N ? (int64_t)r * L : N;
+            lo = bs + splits[(int64_t)r * (n_P + 1) + g];
+            hi = bs + splits[(int64_t)r * (n_P + 1) + g + 1];
+        }
+    }
+    __device__ __forceinline__ int64_t out_base(int64_t g) const
+    {
+        if (kind == 0) {
+            int64_t b = g / gpb, gi = g - b * gpb;
+            int64_t bs = b * L < N ? b * L : N;
+            int64_t be = bs + L < N ? bs + L : N;
+            int64_t s = bs + gi * K * W;
+            return s < be ? s : be;
+        }
+        return offsets[g];
+    }
+    // number of elements of group g
+    __device__ __forceinline__ int64_t size(int64_t g) const
+    {
+        if (kind == 0) {
+            int64_t b = g / gpb;
+            int64_t bs = b * L < N ? b * L : N;
+            int64_t be = bs + L < N ? bs + L : N;
+            int64_t s = out_base(g), e = s + (int64_t)K * W;
+            return (e < be ? e : be) - s;
+        }
+        return offsets[g + 1] - offsets[g];
+    }
+};
+
+// Chunks per group: ceil(M / cnom), at most jcap (so that a pool of POOL
+// samples always has at least as many entries as splitters), at least 1.
+__device__ __forceinline__ int64_t chunks_for(int64_t M, int64_t cnom, int64_t jcap)
+{
+    int64_t j = (M + cnom - 1) / cnom;
+    if (j > jcap) j = jcap;
+    return j < 1 ? 1 : j;
+}
+
+// Sizes of all groups -> chunk counts -> exclusive scan (chunk_off[0..G]).
+// One CTA; G may be large (loops with a carry).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_chunk_plan(MergeJob job, int64_t G, int64_t cnom, int64_t jcap,
+                                                   int64_t* chunk_off)
+{
+    int64_t carry = 0;
+    for (int64_t base = 0; base < G; base += NT) {
+        int64_t g = base + threadIdx.x;
+        int64_t j = 0;
+        if (g < G) j = chunks_for(job.size(g), cnom, jcap);
+        int64_t tot;
+        int64_t ex = block_exscan<NT>(j, &tot);
+        if (g < G) chunk_off[g] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) chunk_off[G] = carry;
+}
+
+template <typename K> struct Splitter {
+    K key;
+    uint32_t run;
+    uint32_t pos;  // position of the splitter inside its run (from the run start)
+};
+
+// Per group: sample every S-th element of every run (S chosen so that the
+// pool has at most POOL entries), sort the pool in shared memory (a multiway
+// merge of the per-run sample lists), and take J-1 splitters at evenly spaced
+// pool ranks.  Chunk j of the group ends with splitter j+1 (inclusive).
+template <int NT, int E, typename K>
+__global__ void __launch_bounds__(NT) k_pool(MergeJob job, GBuf<K> src, const int64_t* chunk_off,
+                                             int* chunk_group, Splitter<K>* spl)
+{
+    constexpr int POOL = NT * E;
+    extern __shared__ __align__(16) char smem[];
+    const int64_t g = blockIdx.x;
+    const int64_t c0 = chunk_off[g];
+    const int64_t J = chunk_off[g + 1] - c0;
+    for (int64_t j = threadIdx.x; j < J; j += NT) chunk_group[c0 + j] = (int)g;
+    if (J <= 1) return;
+    const int Kr = job.K;
+    char* sp = smem;
+    STagged<K> pool{SBuf<K>::carve(sp, POOL), SBuf<uint64_t>::carve(sp, POOL)};
+    int64_t* rlo = (int64_t*)sp;
+    sp += sizeof(int64_t) * Kr;
+    int* off = (int*)sp;
+    for (int r = threadIdx.x; r < Kr; r += NT) {
+        int64_t lo, hi;
+        job.run(g, r, lo, hi);
+        rlo[r] = lo;
+    }
+    const int64_t M = job.size(g);
+    const int64_t S = M <= POOL ? 1 : (M + POOL - 1) / POOL;
+    // per-run sample counts -> piece offsets (runs in contiguous per-thread ranges)
+    const int per = (Kr + NT - 1) / NT;
+    const int r0 = threadIdx.x * per;
+    int64_t mine = 0;
+    for (int r = r0; r < r0 + per && r < Kr; r++) {
+        int64_t lo, hi;
+        job.run(g, r, lo, hi);
+        mine += (hi - lo) / S;
+    }
+    int64_t P64;
+    int64_t ex = block_exscan<NT>(mine, &P64);
+    for (int r = r0; r < r0 + per && r < Kr; r++) {
+        int64_t lo, hi;
+        job.run(g, r, lo, hi);
+        off[r] = (int)ex;
+        ex += (hi - lo) / S;
+    }
+    if (threadIdx.x == 0) off[Kr] = (int)P64;
+    __syncthreads();
+    const int P = (int)P64;
+    for (int i = threadIdx.x; i < P; i += NT) {
+        int a = 0, b = Kr - 1;  // run holding pool slot i: last r with off[r] <= i
+        while (a < b) {
+            int m = (a + b + 1) >> 1;
+            if (off[m] <= i) a = m;
+            else b = m - 1;
+        }
+        int64_t q = (int64_t)(i - off[a]) * S + (S - 1);
+        pool.st(i, Tagged<K>{src.ld(rlo[a] + q), ((uint64_t)a << 32) | (uint64_t)q});
+    }
+    __syncthreads();
+    merge_pieces<NT, E>(pool, off, Kr, P);
+    if (P == 0) return;  // cannot happen when J <= jcap; the co-rank step then clamps
+    for (int64_t j = 1 + threadIdx.x; j < J; j += NT) {
+        int64_t q = (j * (int64_t)P) / J - 1;
+        if (q < 0) q = 0;
+        if (q > P - 1) q = P - 1;
+        Tagged<K> e = pool.ld((int)q);
+        spl[c0 + j] = Splitter<K>{e.key, (uint32_t)(e.tag >> 32), (uint32_t)e.tag};
+    }
+}
+
+// Co-ranks: for chunk c (not the first of its group) and run r, the number of
+// run-r elements that precede chunk c in the order (key, run, position):
+// runs before the splitter's run contribute their elements <= key, runs after
+// it their elements < key, the splitter's own run everything up to and
+// including the splitter.  cr[c*K + r] holds the absolute start index.
+template <typename K>
+__global__ void k_corank(MergeJob job, GBuf<K> src, const Splitter<K>* spl, const int64_t* chunk_off,
+                         const int* chunk_group, const int64_t* nchunks, int64_t* cr)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Kr = job.K;
+    const int64_t c = idx / Kr;
+    const int r = (int)(idx - c * Kr);
+    if (c >= *nchunks) return;
+    const int64_t g = chunk_group[c];
+    int64_t lo, hi;
+    job.run(g, r, lo, hi);
+    int64_t v;
+    if (c == chunk_off[g]) {
+        v = lo;
+    } else {
+        Splitter<K> e = spl[c];
+        if ((uint32_t)r < e.run) v = lo + bound<false>(src, lo, hi, e.key);
+        else if ((uint32_t)r > e.run) v = lo + bound<true>(src, lo, hi, e.key);
+        else v = lo + (int64_t)e.pos + 1;
+        v = v < lo ? lo : (v > hi ? hi : v);
+    }
+    cr[c * Kr + r] = v;
+}
+
+// Smallest key v such that the windows [a[r], b[r]) of sorted runs hold at
+// least t elements <= v (t >= 1): bisection over the key's value domain,
+// each step counting with one binary search per run (Sec. 2.3).  Runs are
+// handled by threads in contiguous ranges; all threads get the result.
+template <int NT, typename K>
+__device__ K select_value(const GBuf<K>& src, const int64_t* a, const int64_t* b, int nruns, int64_t t)
+{
+    using U = typename KT<K>::U;
+    U lo = 0, hi = KT<K>::umax();
+    const int per = (nruns + NT - 1) / NT;
+    const int r0 = threadIdx.x * per;
+    while (lo < hi) {
+        U mid = lo + ((hi - lo) >> 1);
+        K vm = KT<K>::from_u(mid);
+        int64_t cnt = 0;
+        for (int r = r0; r < r0 + per && r < nruns; r++) cnt += bound<false>(src, a[r], b[r], vm);
+        cnt = block_sum<NT>(cnt);
+        if (cnt >= t) hi = mid;
+        else lo = mid + 1;
+    }
+    return KT<K>::from_u(lo);
+}
+
+// Exact co-ranks x[r] in windows [a[r], b[r]) such that the t smallest
+// elements (order: key, run, position) are exactly the prefixes [a[r], x[r]).
+// Copies of the boundary value are taken from runs in run order.
+template <int NT, typename K>
+__device__ void exact_corank(const GBuf<K>& src, const int64_t* a, const int64_t* b, int nruns, int64_t t,
+                             int64_t* x)
+{
+    const int per = (nruns + NT - 1) / NT;
+    const int r0 = threadIdx.x * per;
+    if (t <= 0) {
+        for (int r = r0; r < r0 + per && r < nruns; r++) x[r] = a[r];
+        __syncthreads();
+        return;
+    }
+    K v = select_value<NT, K>(src, a, b, nruns, t);
+    int64_t lbs = 0, eqs = 0;
+    for (int r = r0; r < r0 + per && r < nruns; r++) {
+        int64_t lb = bound<true>(src, a[r], b[r], v);
+        int64_t ub = bound<false>(src, a[r], b[r], v);
+        lbs += lb;
+        eqs += ub - lb;
+    }
+    const int64_t below = block_sum<NT>(lbs);
+    int64_t tot;
+    int64_t pre = block_exscan<NT>(eqs, &tot);
+    const int64_t need = t - below;
+    for (int r = r0; r < r0 + per && r < nruns; r++) {
+        int64_t lb = bound<true>(src, a[r], b[r], v);
+        int64_t eq = bound<false>(src, a[r], b[r], v) - lb;
+        int64_t rem = need - pre;
+        if (rem < 0) rem = 0;
+        int64_t take = eq < rem ? eq : rem;
+        pre += eq;
+        x[r] = a[r] + lb + take;
+    }
+    __syncthreads();
+}
+
+// Merge one chunk per CTA.  The chunk's windows come from the co-rank table;
+// if the chunk holds more than NT*E elements it is cut into exact sub-chunks
+// (exact_corank) and merged piece by piece.  Output keys pass through the
+// inverse transform XF.
+template <int NT, int E, typename K, int XF>
+__global__ void __launch_bounds__(NT) k_merge(MergeJob job, GBuf<K> src, GBuf<K> dst, const int64_t* cr,
+                                              const int64_t* chunk_off, const int* chunk_group,
+                                              const int64_t* nchunks)
+{
+    constexpr int CAP = NT * E;
+    extern __shared__ __align__(16) char smem[];
+    const int64_t c = blockIdx.x;
+    if (c >= *nchunks) return;
+    const int Kr = job.K;
+    const int64_t g = chunk_group[c];
+    const bool last = c + 1 >= chunk_off[g + 1];
+    char* sp = smem;
+    SBuf<K> sb = SBuf<K>::carve(sp, CAP);
+    int64_t* a = (int64_t*)sp;
+    int64_t* b = a + Kr;
+    int64_t* x = b + Kr;
+    int* off = (int*)(x + Kr);
+    int64_t before = 0, msum = 0;
+    for (int r = threadIdx.x; r < Kr; r += NT) {
+        int64_t lo, hi;
+        job.run(g, r, lo, hi);
+        int64_t s = cr[c * Kr + r];
+        int64_t e = last ? hi : cr[(c + 1) * Kr + r];
+        if (e < s) e = s;
+        a[r] = s;
+        b[r] = e;
+        before += s - lo;
+        msum += e - s;
+    }
+    int64_t out = job.out_base(g) + block_sum<NT>(before);
+    int64_t M = block_sum<NT>(msum);
+    if (out < 0 || M < 0 || out + M > job.N) return;  // never write outside the output
+    const int per = (Kr + NT - 1) / NT;
+    const int r0 = threadIdx.x * per;
+    while (M > 0) {
+        const int64_t take = M <= CAP ? M : CAP;
+        if (M <= CAP) {
+            for (int r = threadIdx.x; r < Kr; r += NT) x[r] = b[r];
+            __syncthreads();
+        } else {
+            exact_corank<NT, K>(src, a, b, Kr, take, x);
+        }
+        int64_t mine = 0;
+        for (int r = r0; r < r0 + per && r < Kr; r++) mine += x[r] - a[r];
+        int64_t tot;
+        int64_t ex = block_exscan<NT>(mine, &tot);
+        for (int r = r0; r < r0 + per && r < Kr; r++) {
+            off[r] = (int)ex;
+            ex += x[r] - a[r];
+        }
+        if (threadIdx.x == 0) off[Kr] = (int)take;
+        __syncthreads();
+        for (int i = threadIdx.x; i < (int)take; i += NT) {
+            int lo = 0, hi = Kr - 1;  // piece holding slot i: last r with off[r] <= i
+            while (lo < hi) {
+                int m = (lo + hi + 1) >> 1;
+                if (off[m] <= i) lo = m;
+                else hi = m - 1;
+            }
+            sb.st(i, src.ld(a[lo] + (i - off[lo])));
+        }
+        __syncthreads();
+        merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
+        for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
+        out += take;
+        M -= take;
+        for (int r = threadIdx.x; r < Kr; r += NT) a[r] = x[r];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ step 2 and 3
+// Regular sampling (Sec. 2.3): sample j (1..n_P-1) of non-empty sorted block
+// b of length m is block[floor(j*m/n_P)].  Trailing blocks are the only
+// empty ones, so the non-empty blocks are b < nb1.
+template <typename K>
+__global__ void k_psrs_samples(GBuf<K> blk, GBuf<K> samples, int64_t N, int64_t L, int64_t nb1, int64_t n_P)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = n_P - 1;
+    if (idx >= nb1 * per) return;
+    const int64_t b = idx / per, j = idx - b * per + 1;
+    const int64_t bs = b * L, be = bs + L < N ? bs + L : N;
+    const int64_t m = be - bs;
+    const int64_t pos = (int64_t)(((unsigned __int128)j * (uint64_t)m) / (uint64_t)n_P);
+    samples.st(idx, blk.ld(bs + pos));
+}
+
+// PSRS pivot k = element of rank (k-1)*nb1 + floor((nb1-1)/2) of the sorted
+// pool of samples; the pool is nb1 sorted lists, so the rank is found by the
+// same value bisection as exact splitting, without sorting the pool.
+template <int NT, typename K>
+__global__ void __launch_bounds__(NT) k_psrs_select(GBuf<K> samples, int64_t nb1, int64_t n_P, K* piv)
+{
+    extern __shared__ __align__(16) char smem[];
+    int64_t* a = (int64_t*)smem;
+    int64_t* b = a + nb1;
+    const int64_t k = blockIdx.x + 1;
+    const int64_t per = n_P - 1;
+    for (int64_t r = threadIdx.x; r < nb1; r += NT) {
+        a[r] = r * per;
+        b[r] = (r + 1) * per;
+    }
+    __syncthreads();
+    const int64_t q = (k - 1) * nb1 + (nb1 - 1) / 2;
+    K v = select_value<NT, K>(samples, a, b, (int)nb1, q + 1);
+    if (threadIdx.x == 0) piv[k - 1] = v;
+}
+
+// PSRS splits: s[b][k] = number of elements <= P_k in sorted block b.
+template <typename K>
+__global__ void k_psrs_splits(GBuf<K> blk, const K* piv, int64_t N, int64_t L, int64_t n_B, int64_t n_P,
+                              int64_t* splits)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_B * (n_P - 1)) return;
+    const int64_t b = idx / (n_P - 1), k = idx - b * (n_P - 1) + 1;
+    const int64_t bs = b * L < N ? b * L : N;
+    const int64_t be = bs + L < N ? bs + L : N;
+    splits[b * (n_P + 1) + k] = bound<false>(blk, bs, be, piv[k - 1]);
+}
+
+// PSES (Sec. 2.3): r_k = floor(k*N/n_P); P_k = smallest v with #{x <= v} >=
+// max(r_k, 1) (Eq. 1); c_k = r_k - #{x < P_k} (Eq. 2); split of block b =
+// #{x < P_k in b} plus the copies of P_k it contributes, taken greedily in
+// block order until c_k copies are placed.  One CTA per pivot.
+template <int NT, typename K>
+__global__ void __launch_bounds__(NT) k_pses(GBuf<K> blk, int64_t N, int64_t L, int64_t n_B, int64_t n_P, K* piv,
+                                             int64_t* cvec, int64_t* splits)
+{
+    extern __shared__ __align__(16) char smem[];
+    int64_t* a = (int64_t*)smem;
+    int64_t* b = a + n_B;
+    const int64_t k = blockIdx.x + 1;
+    for (int64_t r = threadIdx.x; r < n_B; r += NT) {
+        int64_t bs = r * L < N ? r * L : N;
+        a[r] = bs;
+        b[r] = bs + L < N ? bs + L : N;
+    }
+    __syncthreads();
+    const int64_t rk = (int64_t)(((unsigned __int128)k * (uint64_t)N) / (uint64_t)n_P);
+    const K v = select_value<NT, K>(blk, a, b, (int)n_B, rk > 0 ? rk : 1);
+    const int per = (int)((n_B + NT - 1) / NT);
+    const int r0 = threadIdx.x * per;
+    int64_t lbs = 0, eqs = 0;
+    for (int r = r0; r < r0 + per && r < n_B; r++) {
+        int64_t lb = bound<true>(blk, a[r], b[r], v);
+        lbs += lb;
+        eqs += bound<false>(blk, a[r], b[r], v) - lb;
+    }
+    const int64_t below = block_sum<NT>(lbs);
+    int64_t tot;
+    int64_t pre = block_exscan<NT>(eqs, &tot);
+    const int64_t ck = rk - below;
+    for (int r = r0; r < r0 + per && r < n_B; r++) {
+        int64_t lb = bound<true>(blk, a[r], b[r], v);
+        int64_t eq = bound<false>(blk, a[r], b[r], v) - lb;
+        int64_t rem = ck - pre;
+        if (rem < 0) rem = 0;
+        int64_t take = eq < rem ? eq : rem;
+        pre += eq;
+        splits[(int64_t)r * (n_P + 1) + k] = lb + take;
+    }
+    if (threadIdx.x == 0) {
+        piv[k - 1] = v;
+        cvec[k - 1] = ck;
+    }
+}
+
+// Split-table borders: s[b][0] = 0 and s[b][n_P] = block length.
+template <int DUMMY = 0>
+__global__ void k_split_borders(int64_t N, int64_t L, int64_t n_B, int64_t n_P, int64_t* splits)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_B) return;
+    const int64_t bs = b * L < N ? b * L : N;
+    const int64_t be = bs + L < N ? bs + L : N;
+    splits[b * (n_P + 1)] = 0;
+    splits[b * (n_P + 1) + n_P] = be - bs;
+}
+
+// O_k = sum over blocks of s[b][k]: the elements of partitions 0..k-1, i.e.
+// the exclusive scan of the partition totals (Sec. 2), for k = 0..n_P.
+template <int DUMMY = 0>
+__global__ void k_offsets(const int64_t* splits, int64_t n_B, int64_t n_P, int64_t* offsets)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n_P) return;
+    int64_t s = 0;
+    for (int64_t b = 0; b < n_B; b++) s += splits[b * (n_P + 1) + k];
+    offsets[k] = s;
+}
+
+// Trace output: pivots back in the caller's representation.
+template <typename K, int XF>
+__global__ void k_trace_pivots(const K* piv, int64_t n, GBuf<K> out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out.template stx<XF>(i, piv[i]);
+}
+
+}  // namespace ps

@@ -1,0 +1,7 @@
+// psort_u64.cu -- kernels and pipeline instantiated for the uint64_t key family.
+#include "psort_pipeline.cuh"
+
+namespace ps {
+int run_sort_u64(const SortArgs& a) { return Pipeline<uint64_t>::run(a); }
+size_t ws_bytes_u64(int64_t n, int64_t n_B, int64_t n_P) { return Pipeline<uint64_t>::ws_bytes(n, n_B, n_P); }
+}  // namespace ps

@@ -1,0 +1,75 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every function
+include/psort.h declares, and rejects bad arguments before touching a GPU."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2305_05245_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "psort.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*|void)\s+(ps_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_function(lib):
+    names = header_functions()
+    assert "ps_sort" in names and "ps_sort_pairs" in names
+    for n in names:
+        assert hasattr(lib, n), "libpsort.so does not export %s" % n
+    from paper_2305_05245_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == sorted(n for n in names if n in _lib.EXPORTS)
+
+
+def test_status_strings(lib):
+    assert lib.ps_status_string(0) == b"ok"
+    for s in range(-7, 0):
+        assert lib.ps_status_string(s) and lib.ps_status_string(s) != b"unknown status"
+    assert lib.ps_status_string(-99) == b"unknown status"
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_2305_05245_gb300 import _lib
+    p = _lib.PsParams()
+    # negative size, bad dtype, bad mode, params out of range
+    assert lib.ps_sort(None, -1, 0, 0, None) == -1
+    assert lib.ps_sort(None, 10, 9, 0, None) == -2
+    assert lib.ps_sort(None, 10, 0, 7, None) == -2
+    p.n_blocks = 5000
+    assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
+    p.n_blocks, p.n_parts = 4, (1 << 20) + 1
+    assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
+    p.n_parts, p.reserved[0] = 4, 1
+    assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
+    # null keys with n >= 2, misaligned keys
+    assert lib.ps_sort(None, 10, 0, 0, None) == -1
+    assert lib.ps_sort(ctypes.c_void_p(0x1002), 10, 1, 0, None) == -1
+    assert lib.ps_sort_pairs(ctypes.c_void_p(0x1000), None, 10, 0, None, None, None) == -1
+    # n = 0 and n = 1 are no-ops
+    assert lib.ps_sort(None, 0, 0, 0, None) == 0
+    assert lib.ps_sort(None, 1, 3, 1, None) == 0
+    assert lib.ps_sort_host(None, 1, 0, 0, None, None) == 0
+    assert lib.ps_sort_host(None, 5, 0, 0, None, None) == -1
+
+
+def test_resolve_and_workspace(lib):
+    import paper_2305_05245_gb300 as ps
+    nb, np_ = ps.resolve_params(1 << 26, 0)
+    assert 1 <= nb <= 4096 and 1 <= np_ <= (1 << 20)
+    assert ps.resolve_params(1 << 20, 0, 64, 64) == (64, 64)
+    w32 = ps.workspace_bytes(1 << 20, 0, 64, 64)
+    w64 = ps.workspace_bytes(1 << 20, 1, 64, 64)
+    assert w32 >= 4 << 20 and w64 >= 8 << 20 and w64 > w32
+    assert ps.workspace_bytes(1, 0) == 0

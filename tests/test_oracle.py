@@ -205,3 +205,22 @@ def test_rejects_bad_arguments(ora):
         ora.sort(np.zeros(4, np.int32), 0, 0, 2)
     with pytest.raises(ValueError):
         ora.sort(np.zeros(4, np.int32), 3, 2, 2)
+
+
+@pytest.mark.parametrize("dtype,dist", [("int32", "uniform"), ("int64", "few_unique"),
+                                        ("float32", "gaussian"), ("float64", "gaussian"),
+                                        ("uint32", "three_valued"), ("uint64", "reverse")])
+def test_reference_sort_matches_oracle(ora, dtype, dist):
+    """The numpy plain-definition reference agrees with the four-step oracle."""
+    if dist == "gaussian" and not dtype.startswith("float"):
+        pytest.skip("gaussian keys are floating point")
+    a = synth.keys(30000, dtype, dist, seed=synth.seed_for("ref", dtype, dist))
+    if dtype.startswith("float"):
+        a[:4] = [-0.0, 0.0, -0.0, 0.0]
+    got = ora.reference_sort(a)
+    want = ora.sort(a, 1, 7, 9).out
+    assert got.tobytes() == want.tobytes()
+    k, p = synth.records(5000, seed=3, dist="few_unique")
+    rk, rp = ora.reference_sort(k, p)
+    r = ora.sort(k, 0, 5, 5, payload=p)
+    assert np.array_equal(rk, r.out) and np.array_equal(rp, r.out_payload)
