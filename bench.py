@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--n-parts", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1 << 23)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 25)
     return ap.parse_args()
 
 

@@ -1,6 +1,8 @@
 // psort_api.cu -- the C ABI declared in include/psort.h: argument checks,
 // automatic parameters, the workspace pool, and dispatch to the key families.
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -124,16 +126,23 @@ static int64_t pow2_floor(int64_t x)
     return p;
 }
 
-// Size-binned defaults: blocks of about 2^19 keys (2^18 for records), at
-// most 1024 blocks; partitions of about 2^17 keys.
+// Size-binned defaults.  The block sort makes in-block merge passes of
+// fan-in <= 256 over tiles of T keys and the final merge has fan-in n_B; on
+// GB300 the measured optimum sits near n_B = 0.35 * sqrt(N / T) (64 blocks at
+// 2^28 keys, 128 at 2^30).  Exact splitting costs O(n_P * n_B * log^2 L)
+// probes (Sec. 2.3), so n_P stays <= min(n_B, 256); the final merge cuts
+// partitions into chunks on its own.
 static void resolve(int64_t n, int dtype, const ps_params* in, ps_params* out)
 {
     ps_params r;
     memset(&r, 0, sizeof(r));
     if (in) r = *in;
-    const int64_t blk = dtype < 0 ? (1 << 18) : (1 << 19);
-    if (r.n_blocks <= 0) r.n_blocks = std::min<int64_t>(1024, std::max<int64_t>(1, pow2_floor(n / blk)));
-    if (r.n_parts <= 0) r.n_parts = std::min<int64_t>(4096, std::max<int64_t>(1, pow2_floor(n / (1 << 17))));
+    const double tile = dtype < 0 ? 4096.0 : 8192.0;
+    const double want = 0.35 * std::sqrt((double)n / tile);
+    int64_t nb = 1;
+    while (nb < 1024 && (double)nb * 1.41421356 < want) nb *= 2;
+    if (r.n_blocks <= 0) r.n_blocks = nb;
+    if (r.n_parts <= 0) r.n_parts = std::min<int64_t>(256, std::max<int64_t>(1, r.n_blocks));
     *out = r;
 }
 

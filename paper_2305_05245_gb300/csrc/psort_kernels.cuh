@@ -93,6 +93,9 @@ template <int XF> __device__ __forceinline__ uint64_t kappa_inv(uint64_t k)
     return k;
 }
 
+template <int XF> __device__ __forceinline__ uint32_t xform(uint32_t x) { return kappa<XF>(x); }
+template <int XF> __device__ __forceinline__ uint64_t xform(uint64_t x) { return kappa<XF>(x); }
+
 // ------------------------------------------------------------ global buffers
 template <typename K> struct GBuf;
 template <> struct GBuf<uint32_t> {
@@ -117,6 +120,8 @@ template <> struct GBuf<Rec> {
     template <int XF> __device__ Rec ldx(int64_t i) const { return Rec{k[i], p[i]}; }
     template <int XF> __device__ void stx(int64_t i, const Rec& v) const { k[i] = v.k; p[i] = v.p; }
 };
+
+template <int XF> __device__ __forceinline__ Rec xform(const Rec& x) { return x; }
 
 // ---------------------------------------------- shared-memory buffers (padded)
 // One pad slot after every 128 bytes, so that thread t reading its E
@@ -150,6 +155,37 @@ template <> struct SBuf<Rec> {
         return b;
     }
 };
+
+// ------------------------------------------- asynchronous global->shared copies
+// cp.async (Ampere-and-later LDGSTS): each thread queues element copies
+// without staging them in registers, so a CTA keeps many loads in flight.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_elem(const SBuf<uint32_t>& s, int i, const GBuf<uint32_t>& g, int64_t j)
+{
+    cp_async4(s.a + i + (i >> 5), g.p + j);
+}
+__device__ __forceinline__ void cp_elem(const SBuf<uint64_t>& s, int i, const GBuf<uint64_t>& g, int64_t j)
+{
+    cp_async8(s.a + i + (i >> 4), g.p + j);
+}
+__device__ __forceinline__ void cp_elem(const SBuf<Rec>& s, int i, const GBuf<Rec>& g, int64_t j)
+{
+    cp_async8(s.k.a + i + (i >> 4), g.k + j);
+    cp_async4(s.p.a + i + (i >> 5), g.p + j);
+}
 
 // Storage views used by the merge routine: plain keys, or keys carrying a
 // 64-bit tag (run index and position of a pool sample).  Comparison is on
@@ -273,68 +309,132 @@ template <int E, typename K> __device__ __forceinline__ void reg_sort(K (&r)[E])
 }
 
 // -------------------------------------------- shared-memory multiway merge
-// The n elements of `s` form P sorted pieces with boundaries off[0..P]
-// (off[0] = 0, off[P] = n, in shared memory).  Pairs of adjacent units are
-// merged level by level (merge path: each thread finds where its E outputs
-// start by binary search, then merges them serially); after ceil(log2 P)
-// levels the n elements are one sorted run, in place.  Ties keep the lower
-// piece first.  Requires n <= NT*E.  Called by all threads of the block.
+// Serial merge of E outputs from the heads A[ai..aend) and B[bi..bend) of one
+// merge unit (stable: A wins ties).  Reads one element past an exhausted
+// side, which the buffers' spare slot makes safe.  STOP guards the last
+// partial thread (cnt < E) of a chunk.
+template <int E, bool STOP, typename S>
+__device__ __forceinline__ void serial_merge(const S& s, int ai, int aend, int bi, int bend, int cnt,
+                                             typename S::V (&out)[E])
+{
+    using V = typename S::V;
+    V a = s.ld(ai), b = s.ld(bi);
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        if (!STOP || i < cnt) {
+            const bool p = (bi >= bend) || ((ai < aend) && !S::lt(b, a));
+            out[i] = p ? a : b;
+            const int nx = p ? ai + 1 : bi + 1;
+            const V c = s.ld(nx);
+            if (p) {
+                a = c;
+                ai = nx;
+            } else {
+                b = c;
+                bi = nx;
+            }
+        }
+    }
+}
+
+// Merge-path split of diagonal d of the unit A = [us, um), B = [um, ue):
+// the number of A elements among the unit's first d outputs.
+template <typename S>
+__device__ __forceinline__ int merge_path(const S& s, int us, int um, int ue, int d)
+{
+    int a0 = d - (ue - um) > 0 ? d - (ue - um) : 0;
+    int a1 = d < um - us ? d : um - us;
+    while (a0 < a1) {
+        const int mid = (a0 + a1) >> 1;
+        if (!S::lt(s.ld(um + d - 1 - mid), s.ld(us + mid))) a0 = mid + 1;
+        else a1 = mid;
+    }
+    return a0;
+}
+
+// Tile levels: NT*E elements in pieces of E that double each level (units of
+// U = 2, 4, ... pieces' worth, all powers of two); every thread owns exactly E
+// outputs that never straddle a unit.
+template <int NT, int E, typename S>
+__device__ void merge_levels_pow2(const S& s)
+{
+    using V = typename S::V;
+    const int pos0 = threadIdx.x * E;
+#pragma unroll 1
+    for (int U = 2 * E; U <= NT * E; U <<= 1) {
+        const int us = pos0 & ~(U - 1), um = us + U / 2, ue = us + U;
+        const int x = merge_path(s, us, um, ue, pos0 - us);
+        V out[E];
+        serial_merge<E, false>(s, us + x, um, um + (pos0 - us - x), ue, E, out);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; i++) s.st(pos0 + i, out[i]);
+        __syncthreads();
+    }
+}
+
+// General levels: the n elements of `s` form P sorted pieces with boundaries
+// off[0..P] (off[0] = 0, off[P] = n, in shared memory); adjacent units are
+// merged level by level until one sorted run remains, in place.  At level l a
+// unit is 2^(l+1) consecutive pieces, so the unit holding a position is the
+// position's piece index shifted right by l+1 (found once per thread).  A
+// thread's E outputs may cross into later units; each crossing restarts the
+// merge at the next unit's head.  Ties keep the lower piece first.
+// Requires n <= NT*E.
 template <int NT, int E, typename S>
 __device__ void merge_pieces(const S& s, const int* off, int P, int n)
 {
     using V = typename S::V;
     const int pos0 = threadIdx.x * E;
     const int cnt = n - pos0 < E ? n - pos0 : E;
-    for (int w = 1; w < P; w <<= 1) {
+    int p0 = 0;  // last piece starting at or before pos0
+    if (cnt > 0) {
+        int hi = P - 1;
+        while (p0 < hi) {
+            const int mid = (p0 + hi + 1) >> 1;
+            if (off[mid] <= pos0) p0 = mid;
+            else hi = mid - 1;
+        }
+    }
+    for (int sh = 1; (1 << (sh - 1)) < P; sh++) {
+        const int w = 1 << (sh - 1);
         V out[E];
         if (cnt > 0) {
-            const int nunits = (P + 2 * w - 1) / (2 * w);
-            // the unit holding output position pos0: the last unit starting at or before it
-            int lo = 0, hi = nunits - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                int st = off[min(mid * 2 * w, P)];
-                if (st <= pos0) lo = mid;
-                else hi = mid - 1;
-            }
-            int u = lo;
+            int u = p0 >> sh;
             int us = off[min(u * 2 * w, P)], um = off[min(u * 2 * w + w, P)], ue = off[min(u * 2 * w + 2 * w, P)];
-            // merge path inside unit u: how many of the first d outputs come from A
-            const int d = pos0 - us, alen = um - us, blen = ue - um;
-            int a0 = d - blen > 0 ? d - blen : 0, a1 = d < alen ? d : alen;
-            while (a0 < a1) {
-                int mid = (a0 + a1) >> 1;
-                if (!S::lt(s.ld(um + d - 1 - mid), s.ld(us + mid))) a0 = mid + 1;
-                else a1 = mid;
-            }
-            int ai = us + a0, bi = um + d - a0;
-            V av = s.ld(ai < um ? ai : us);
-            V bv = s.ld(bi < ue ? bi : um);
+            const int x = merge_path(s, us, um, ue, pos0 - us);
+            int ai = us + x, bi = um + (pos0 - us - x);
+            int left = ue - pos0;  // outputs left in this unit
+            V a = s.ld(ai), b = s.ld(bi);
 #pragma unroll
             for (int i = 0; i < E; i++) {
                 if (i < cnt) {
-                    if (ai >= um && bi >= ue) {
+                    if (left == 0) {
                         // this unit is exhausted: continue with the next non-empty unit
                         do {
                             u++;
                             us = ue;
                             um = off[min(u * 2 * w + w, P)];
                             ue = off[min(u * 2 * w + 2 * w, P)];
-                        } while (us == ue && u < nunits);
+                        } while (us == ue && ue < n);
                         ai = us;
                         bi = um;
-                        av = s.ld(ai < um ? ai : us);
-                        bv = s.ld(bi < ue ? bi : um);
+                        left = ue - us;
+                        a = s.ld(ai);
+                        b = s.ld(bi);
                     }
-                    bool ta = ai < um && (bi >= ue || !S::lt(bv, av));
-                    out[i] = ta ? av : bv;
-                    if (ta) {
-                        ai++;
-                        if (ai < um) av = s.ld(ai);
+                    const bool p = (bi >= ue) || ((ai < um) && !S::lt(b, a));
+                    out[i] = p ? a : b;
+                    const int nx = p ? ai + 1 : bi + 1;
+                    const V c = s.ld(nx);
+                    if (p) {
+                        a = c;
+                        ai = nx;
                     } else {
-                        bi++;
-                        if (bi < ue) bv = s.ld(bi);
+                        b = c;
+                        bi = nx;
                     }
+                    left--;
                 }
             }
         }
@@ -376,24 +476,26 @@ __global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, int6
     extern __shared__ __align__(16) char smem[];
     char* sp = smem;
     SBuf<K> sb = SBuf<K>::carve(sp, T);
-    int* off = (int*)sp;
     const int64_t b = blockIdx.x / tiles_per_block, t = blockIdx.x - b * tiles_per_block;
     const int64_t bs = b * L < N ? b * L : N;
     const int64_t be = bs + L < N ? bs + L : N;
     const int64_t ts = bs + t * T;
     if (ts >= be) return;
     const int n = (int)(be - ts < T ? be - ts : T);
-    for (int i = threadIdx.x; i < T; i += NT) sb.st(i, i < n ? src.template ldx<XF>(ts + i) : KT<K>::maxkey());
-    for (int i = threadIdx.x; i <= NT; i += NT) off[i] = i * E;
+    for (int i = threadIdx.x; i < n; i += NT) cp_elem(sb, i, src, ts + i);
+    cp_async_wait_all();
     __syncthreads();
     K r[E];
 #pragma unroll
-    for (int j = 0; j < E; j++) r[j] = sb.ld(threadIdx.x * E + j);
+    for (int j = 0; j < E; j++) {
+        const int i = threadIdx.x * E + j;
+        r[j] = i < n ? xform<XF>(sb.ld(i)) : KT<K>::maxkey();
+    }
     reg_sort<E>(r);
 #pragma unroll
     for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
     __syncthreads();
-    merge_pieces<NT, E>(SKeys<K>{sb}, off, NT, T);
+    merge_levels_pow2<NT, E>(SKeys<K>{sb});
     for (int i = threadIdx.x; i < n; i += NT) dst.st(ts + i, sb.ld(i));
 }
 
@@ -452,8 +554,40 @@ struct MergeJob {
     }
 };
 
-// Chunks per group: ceil(M / cnom), at most jcap (so that a pool of POOL
-// samples always has at least as many entries as splitters), at least 1.
+// Window table of one refinement level: group g merges the K sorted runs
+// [lo[g*K + r], hi[g*K + r]) of the source into [base[g], base[g] + size[g])
+// of the destination; *ng groups exist (a device-side count).
+struct Level {
+    int K;
+    int64_t* lo;
+    int64_t* hi;
+    int64_t* base;
+    int64_t* size;
+    int64_t* ng;
+};
+
+// Level 0 of a merge job: its groups' runs, output bases and sizes.
+template <int DUMMY = 0>
+__global__ void k_root_windows(MergeJob job, int64_t G, Level L)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G * job.K) return;
+    const int64_t g = idx / job.K;
+    const int r = (int)(idx - g * job.K);
+    int64_t lo, hi;
+    job.run(g, r, lo, hi);
+    if (hi < lo) hi = lo;
+    L.lo[idx] = lo;
+    L.hi[idx] = hi;
+    if (r == 0) {
+        L.base[g] = job.out_base(g);
+        L.size[g] = job.size(g);
+    }
+    if (idx == 0) *L.ng = G;
+}
+
+// Children per group: ceil(M / cnom), at most jcap (so that the sample pool
+// always holds more samples than splitters), at least 1.
 __device__ __forceinline__ int64_t chunks_for(int64_t M, int64_t cnom, int64_t jcap)
 {
     int64_t j = (M + cnom - 1) / cnom;
@@ -461,150 +595,234 @@ __device__ __forceinline__ int64_t chunks_for(int64_t M, int64_t cnom, int64_t j
     return j < 1 ? 1 : j;
 }
 
-// Sizes of all groups -> chunk counts -> exclusive scan (chunk_off[0..G]).
+// Child counts of every group of a level -> exclusive scan choff[0..G].
 // One CTA; G may be large (loops with a carry).
 template <int NT>
-__global__ void __launch_bounds__(NT) k_chunk_plan(MergeJob job, int64_t G, int64_t cnom, int64_t jcap,
-                                                   int64_t* chunk_off)
+__global__ void __launch_bounds__(NT) k_chunk_plan(Level L, int64_t cnom, int64_t jcap, int64_t* choff)
 {
+    const int64_t G = *L.ng;
     int64_t carry = 0;
     for (int64_t base = 0; base < G; base += NT) {
-        int64_t g = base + threadIdx.x;
-        int64_t j = 0;
-        if (g < G) j = chunks_for(job.size(g), cnom, jcap);
+        const int64_t g = base + threadIdx.x;
+        const int64_t j = g < G ? chunks_for(L.size[g], cnom, jcap) : 0;
         int64_t tot;
-        int64_t ex = block_exscan<NT>(j, &tot);
-        if (g < G) chunk_off[g] = carry + ex;
+        const int64_t ex = block_exscan<NT>(j, &tot);
+        if (g < G) choff[g] = carry + ex;
         carry += tot;
     }
-    if (threadIdx.x == 0) chunk_off[G] = carry;
+    if (threadIdx.x == 0) choff[G] = carry;
 }
 
 template <typename K> struct Splitter {
     K key;
     uint32_t run;
-    uint32_t pos;  // position of the splitter inside its run (from the run start)
+    uint32_t pos;  // position of the splitter inside its run (from the window start)
 };
 
-// Per group: sample every S-th element of every run (S chosen so that the
-// pool has at most POOL entries), sort the pool in shared memory (a multiway
-// merge of the per-run sample lists), and take J-1 splitters at evenly spaced
-// pool ranks.  Chunk j of the group ends with splitter j+1 (inclusive).
+// Per group: cut every run into blocks of S elements (the last block of a run
+// may be shorter) and take each block's last element as a sample standing for
+// the block's keys; S is chosen so that the pool holds about J*max(2K, 96)
+// samples (at most POOL).
+// The pool is sorted in shared memory (a multiway merge of the per-run sample
+// lists, stable, so ties order by run then position).  Splitter j (1..J-1) is
+// the first sample whose cumulative weight reaches j*M/J; child j-1 ends with
+// it (inclusive) and child j starts after it.
 template <int NT, int E, typename K>
-__global__ void __launch_bounds__(NT) k_pool(MergeJob job, GBuf<K> src, const int64_t* chunk_off,
-                                             int* chunk_group, Splitter<K>* spl)
+__global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t* choff, int* chgrp,
+                                             Splitter<K>* spl)
 {
     constexpr int POOL = NT * E;
     extern __shared__ __align__(16) char smem[];
     const int64_t g = blockIdx.x;
-    const int64_t c0 = chunk_off[g];
-    const int64_t J = chunk_off[g + 1] - c0;
-    for (int64_t j = threadIdx.x; j < J; j += NT) chunk_group[c0 + j] = (int)g;
+    if (g >= *L.ng) return;
+    const int64_t c0 = choff[g];
+    const int64_t J = choff[g + 1] - c0;
+    for (int64_t j = threadIdx.x; j < J; j += NT) chgrp[c0 + j] = (int)g;
     if (J <= 1) return;
-    const int Kr = job.K;
+    const int Kr = L.K;
+    const int64_t* lo = L.lo + g * Kr;
+    const int64_t* hi = L.hi + g * Kr;
     char* sp = smem;
     STagged<K> pool{SBuf<K>::carve(sp, POOL), SBuf<uint64_t>::carve(sp, POOL)};
-    int64_t* rlo = (int64_t*)sp;
-    sp += sizeof(int64_t) * Kr;
     int* off = (int*)sp;
-    for (int r = threadIdx.x; r < Kr; r += NT) {
-        int64_t lo, hi;
-        job.run(g, r, lo, hi);
-        rlo[r] = lo;
-    }
-    const int64_t M = job.size(g);
-    const int64_t S = M <= POOL ? 1 : (M + POOL - 1) / POOL;
-    // per-run sample counts -> piece offsets (runs in contiguous per-thread ranges)
+    const int64_t M = L.size[g];
+    // about max(2K, 96) samples per child: enough to place every splitter
+    // within a few percent of its target rank (each run's co-rank is known
+    // to within its S-key block), and no more than the pool holds
+    int64_t ptarget = J * (2 * (int64_t)Kr > 96 ? 2 * (int64_t)Kr : 96);
+    if (ptarget > POOL) ptarget = POOL;
+    const int64_t room = ptarget - Kr > 1 ? ptarget - Kr : 1;
+    const int64_t S = M <= room ? 1 : (M + room - 1) / room;
     const int per = (Kr + NT - 1) / NT;
     const int r0 = threadIdx.x * per;
     int64_t mine = 0;
-    for (int r = r0; r < r0 + per && r < Kr; r++) {
-        int64_t lo, hi;
-        job.run(g, r, lo, hi);
-        mine += (hi - lo) / S;
-    }
+    for (int r = r0; r < r0 + per && r < Kr; r++) mine += (hi[r] - lo[r] + S - 1) / S;
     int64_t P64;
     int64_t ex = block_exscan<NT>(mine, &P64);
     for (int r = r0; r < r0 + per && r < Kr; r++) {
-        int64_t lo, hi;
-        job.run(g, r, lo, hi);
         off[r] = (int)ex;
-        ex += (hi - lo) / S;
+        ex += (hi[r] - lo[r] + S - 1) / S;
     }
     if (threadIdx.x == 0) off[Kr] = (int)P64;
     __syncthreads();
-    const int P = (int)P64;
+    const int P = (int)P64;  // <= M/S + K <= POOL
     for (int i = threadIdx.x; i < P; i += NT) {
-        int a = 0, b = Kr - 1;  // run holding pool slot i: last r with off[r] <= i
-        while (a < b) {
-            int m = (a + b + 1) >> 1;
-            if (off[m] <= i) a = m;
-            else b = m - 1;
+        int x = 0, y = Kr - 1;  // run holding pool slot i: last r with off[r] <= i
+        while (x < y) {
+            const int m = (x + y + 1) >> 1;
+            if (off[m] <= i) x = m;
+            else y = m - 1;
         }
-        int64_t q = (int64_t)(i - off[a]) * S + (S - 1);
-        pool.st(i, Tagged<K>{src.ld(rlo[a] + q), ((uint64_t)a << 32) | (uint64_t)q});
+        int64_t q = (int64_t)(i - off[x]) * S + (S - 1);
+        const int64_t last = hi[x] - lo[x] - 1;
+        if (q > last) q = last;
+        cp_elem(pool.kb, i, src, lo[x] + q);
+        pool.tb.st(i, ((uint64_t)x << 32) | (uint64_t)q);
     }
+    cp_async_wait_all();
     __syncthreads();
     merge_pieces<NT, E>(pool, off, Kr, P);
-    if (P == 0) return;  // cannot happen when J <= jcap; the co-rank step then clamps
-    for (int64_t j = 1 + threadIdx.x; j < J; j += NT) {
-        int64_t q = (j * (int64_t)P) / J - 1;
-        if (q < 0) q = 0;
-        if (q > P - 1) q = P - 1;
-        Tagged<K> e = pool.ld((int)q);
-        spl[c0 + j] = Splitter<K>{e.key, (uint32_t)(e.tag >> 32), (uint32_t)e.tag};
+    // weights: a sample stands for S keys, or for the shorter last block of its run
+    const int q0 = threadIdx.x * E;
+    int64_t wsum = 0;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        if (q0 + i < P) {
+            const uint64_t tag = pool.tb.ld(q0 + i);
+            const int x = (int)(tag >> 32);
+            const int64_t q = (int64_t)(uint32_t)tag, len = hi[x] - lo[x];
+            wsum += (q == len - 1 && len % S) ? len % S : S;
+        }
+    }
+    int64_t tot;
+    int64_t cb = block_exscan<NT>(wsum, &tot);
+    // A splitter's co-rank exceeds its cumulative weight by the partial block
+    // of every other run, (S-1)/2 keys on average: aim the weights that much lower.
+    const int64_t adj = (int64_t)(Kr - 1) * (S - 1) / 2;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        if (q0 + i < P) {
+            const Tagged<K> e = pool.ld(q0 + i);
+            const int x = (int)(e.tag >> 32);
+            const int64_t q = (int64_t)(uint32_t)e.tag, len = hi[x] - lo[x];
+            const int64_t ci = cb + ((q == len - 1 && len % S) ? len % S : S);
+            // splitters j whose target max(1, floor(j*M/J) - adj) lies in (cb, ci]
+            int64_t j = (int64_t)(((unsigned __int128)(cb + adj) * (uint64_t)J) / (uint64_t)M) - 1;
+            if (j < 1) j = 1;
+            for (; j < J; j++) {
+                int64_t t = (int64_t)(((unsigned __int128)j * (uint64_t)M) / (uint64_t)J) - adj;
+                if (t < 1) t = 1;
+                if (t > ci) break;
+                if (t > cb) spl[c0 + j] = Splitter<K>{e.key, (uint32_t)x, (uint32_t)q};
+            }
+            cb = ci;
+        }
     }
 }
 
-// Co-ranks: for chunk c (not the first of its group) and run r, the number of
-// run-r elements that precede chunk c in the order (key, run, position):
-// runs before the splitter's run contribute their elements <= key, runs after
-// it their elements < key, the splitter's own run everything up to and
-// including the splitter.  cr[c*K + r] holds the absolute start index.
+// Co-ranks: for child c (not the first of its group) and run r, where child
+// c starts in run r: runs before the splitter's run contribute their
+// elements <= key, runs after it their elements < key, the splitter's own run
+// everything up to and including the splitter.  Writes the child level's lo.
 template <typename K>
-__global__ void k_corank(MergeJob job, GBuf<K> src, const Splitter<K>* spl, const int64_t* chunk_off,
-                         const int* chunk_group, const int64_t* nchunks, int64_t* cr)
+__global__ void k_corank(Level L, GBuf<K> src, const Splitter<K>* spl, const int64_t* choff, const int* chgrp,
+                         Level C)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Kr = job.K;
+    const int Kr = L.K;
     const int64_t c = idx / Kr;
     const int r = (int)(idx - c * Kr);
-    if (c >= *nchunks) return;
-    const int64_t g = chunk_group[c];
-    int64_t lo, hi;
-    job.run(g, r, lo, hi);
+    if (c >= choff[*L.ng]) return;
+    const int64_t g = chgrp[c];
+    const int64_t lo = L.lo[g * Kr + r], hi = L.hi[g * Kr + r];
     int64_t v;
-    if (c == chunk_off[g]) {
+    if (c == choff[g]) {
         v = lo;
     } else {
-        Splitter<K> e = spl[c];
+        const Splitter<K> e = spl[c];
         if ((uint32_t)r < e.run) v = lo + bound<false>(src, lo, hi, e.key);
         else if ((uint32_t)r > e.run) v = lo + bound<true>(src, lo, hi, e.key);
         else v = lo + (int64_t)e.pos + 1;
         v = v < lo ? lo : (v > hi ? hi : v);
     }
-    cr[c * Kr + r] = v;
+    C.lo[c * Kr + r] = v;
+}
+
+// Child level completion: hi from the next sibling's lo (or the parent's hi
+// for the last child), output base and size.  One CTA per child.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* choff, const int* chgrp, Level C)
+{
+    const int64_t c = blockIdx.x;
+    const int64_t nch = choff[*L.ng];
+    if (c >= nch) return;
+    const int Kr = L.K;
+    const int64_t g = chgrp[c];
+    const bool last = c + 1 >= choff[g + 1];
+    int64_t before = 0, sz = 0;
+    for (int r = threadIdx.x; r < Kr; r += NT) {
+        const int64_t lo = C.lo[c * Kr + r];
+        int64_t hi = last ? L.hi[g * Kr + r] : C.lo[(c + 1) * Kr + r];
+        if (hi < lo) hi = lo;
+        C.hi[c * Kr + r] = hi;
+        before += lo - L.lo[g * Kr + r];
+        sz += hi - lo;
+    }
+    before = block_sum<NT>(before);
+    sz = block_sum<NT>(sz);
+    if (threadIdx.x == 0) {
+        C.base[c] = L.base[g] + before;
+        C.size[c] = sz;
+        if (c == 0) *C.ng = nch;
+    }
 }
 
 // Smallest key v such that the windows [a[r], b[r]) of sorted runs hold at
 // least t elements <= v (t >= 1): bisection over the key's value domain,
-// each step counting with one binary search per run (Sec. 2.3).  Runs are
-// handled by threads in contiguous ranges; all threads get the result.
-template <int NT, typename K>
+// each step counting with one binary search per run (Sec. 2.3).  Each run's
+// search window shrinks with the value interval: elements left of it are
+// known to be <= every remaining candidate, elements right of it are known
+// to be larger.  Runs are handled by threads in contiguous ranges of at most
+// MAXPER; all threads get the result.
+template <int NT, typename K, int MAXPER = 8>
 __device__ K select_value(const GBuf<K>& src, const int64_t* a, const int64_t* b, int nruns, int64_t t)
 {
     using U = typename KT<K>::U;
     U lo = 0, hi = KT<K>::umax();
     const int per = (nruns + NT - 1) / NT;
     const int r0 = threadIdx.x * per;
+    int64_t wa[MAXPER], wb[MAXPER];
+#pragma unroll
+    for (int q = 0; q < MAXPER; q++) {
+        const int r = r0 + q;
+        const bool ok = q < per && r < nruns;
+        wa[q] = ok ? a[r] : 0;
+        wb[q] = ok ? b[r] : 0;
+    }
+    int64_t below = 0;  // this thread's elements left of its windows
     while (lo < hi) {
-        U mid = lo + ((hi - lo) >> 1);
-        K vm = KT<K>::from_u(mid);
-        int64_t cnt = 0;
-        for (int r = r0; r < r0 + per && r < nruns; r++) cnt += bound<false>(src, a[r], b[r], vm);
+        const U mid = lo + ((hi - lo) >> 1);
+        const K vm = KT<K>::from_u(mid);
+        int64_t c[MAXPER];
+        int64_t cnt = below;
+#pragma unroll
+        for (int q = 0; q < MAXPER; q++) {
+            c[q] = bound<false>(src, wa[q], wb[q], vm);
+            cnt += c[q];
+        }
         cnt = block_sum<NT>(cnt);
-        if (cnt >= t) hi = mid;
-        else lo = mid + 1;
+        if (cnt >= t) {
+            hi = mid;
+#pragma unroll
+            for (int q = 0; q < MAXPER; q++) wb[q] = wa[q] + c[q];
+        } else {
+            lo = mid + 1;
+#pragma unroll
+            for (int q = 0; q < MAXPER; q++) {
+                wa[q] += c[q];
+                below += c[q];
+            }
+        }
     }
     return KT<K>::from_u(lo);
 }
@@ -647,79 +865,84 @@ __device__ void exact_corank(const GBuf<K>& src, const int64_t* a, const int64_t
     __syncthreads();
 }
 
-// Merge one chunk per CTA.  The chunk's windows come from the co-rank table;
-// if the chunk holds more than NT*E elements it is cut into exact sub-chunks
-// (exact_corank) and merged piece by piece.  Output keys pass through the
-// inverse transform XF.
-template <int NT, int E, typename K, int XF>
-__global__ void __launch_bounds__(NT) k_merge(MergeJob job, GBuf<K> src, GBuf<K> dst, const int64_t* cr,
-                                              const int64_t* chunk_off, const int* chunk_group,
-                                              const int64_t* nchunks)
+// Merge one group of the last level per CTA (its windows, base and size come
+// from the level's table).  BIG = false: groups of at most NT*E elements are
+// merged in shared memory; larger ones (possible when a sample pool misjudged
+// a split) are appended to `big` and left to the BIG = true launch, which cuts
+// each into exact sub-chunks (exact_corank) and merges those one after another.
+// Output keys pass through the inverse transform XF.
+template <int NT, int E, typename K, int XF, bool BIG>
+__global__ void __launch_bounds__(NT) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
+                                              unsigned long long* nbig)
 {
     constexpr int CAP = NT * E;
     extern __shared__ __align__(16) char smem[];
-    const int64_t c = blockIdx.x;
-    if (c >= *nchunks) return;
-    const int Kr = job.K;
-    const int64_t g = chunk_group[c];
-    const bool last = c + 1 >= chunk_off[g + 1];
+    const int Kr = C.K;
     char* sp = smem;
     SBuf<K> sb = SBuf<K>::carve(sp, CAP);
-    int64_t* a = (int64_t*)sp;
-    int64_t* b = a + Kr;
-    int64_t* x = b + Kr;
-    int* off = (int*)(x + Kr);
-    int64_t before = 0, msum = 0;
-    for (int r = threadIdx.x; r < Kr; r += NT) {
-        int64_t lo, hi;
-        job.run(g, r, lo, hi);
-        int64_t s = cr[c * Kr + r];
-        int64_t e = last ? hi : cr[(c + 1) * Kr + r];
-        if (e < s) e = s;
-        a[r] = s;
-        b[r] = e;
-        before += s - lo;
-        msum += e - s;
-    }
-    int64_t out = job.out_base(g) + block_sum<NT>(before);
-    int64_t M = block_sum<NT>(msum);
-    if (out < 0 || M < 0 || out + M > job.N) return;  // never write outside the output
+    int64_t* a = (int64_t*)sp;                       // window starts
+    int64_t* b = BIG ? a + Kr : nullptr;             // window ends (BIG only)
+    int64_t* x = BIG ? a + 2 * Kr : nullptr;         // sub-chunk ends (BIG only)
+    int* len = (int*)(a + (BIG ? 3 : 1) * Kr);       // piece lengths of the current (sub-)chunk
+    int* off = len + Kr;                             // piece offsets in shared memory
     const int per = (Kr + NT - 1) / NT;
     const int r0 = threadIdx.x * per;
-    while (M > 0) {
-        const int64_t take = M <= CAP ? M : CAP;
-        if (M <= CAP) {
-            for (int r = threadIdx.x; r < Kr; r += NT) x[r] = b[r];
-            __syncthreads();
-        } else {
-            exact_corank<NT, K>(src, a, b, Kr, take, x);
+    const int64_t nwork = BIG ? (int64_t)*nbig : *C.ng;
+    const int64_t stride = BIG ? gridDim.x : (nwork > 0 ? nwork : 1);
+    for (int64_t w = blockIdx.x; w < nwork; w += stride) {
+        const int64_t c = BIG ? big[w] : w;
+        int64_t out = C.base[c];
+        int64_t M = C.size[c];
+        if (out < 0 || M < 0 || out + M > nout) continue;  // never write outside the output
+        if (!BIG && M > CAP) {
+            if (threadIdx.x == 0) big[atomicAdd(nbig, 1ull)] = c;
+            continue;
         }
-        int64_t mine = 0;
-        for (int r = r0; r < r0 + per && r < Kr; r++) mine += x[r] - a[r];
-        int64_t tot;
-        int64_t ex = block_exscan<NT>(mine, &tot);
-        for (int r = r0; r < r0 + per && r < Kr; r++) {
-            off[r] = (int)ex;
-            ex += x[r] - a[r];
+        for (int r = threadIdx.x; r < Kr; r += NT) {
+            a[r] = C.lo[c * Kr + r];
+            if constexpr (BIG) b[r] = C.hi[c * Kr + r];
+            else len[r] = (int)(C.hi[c * Kr + r] - C.lo[c * Kr + r]);
         }
-        if (threadIdx.x == 0) off[Kr] = (int)take;
         __syncthreads();
-        for (int i = threadIdx.x; i < (int)take; i += NT) {
-            int lo = 0, hi = Kr - 1;  // piece holding slot i: last r with off[r] <= i
-            while (lo < hi) {
-                int m = (lo + hi + 1) >> 1;
-                if (off[m] <= i) lo = m;
-                else hi = m - 1;
+        while (M > 0) {
+            const int64_t take = M <= CAP ? M : CAP;
+            if constexpr (BIG) {
+                if (M > CAP) exact_corank<NT, K>(src, a, b, Kr, take, x);
+                else {
+                    for (int r = threadIdx.x; r < Kr; r += NT) x[r] = b[r];
+                    __syncthreads();
+                }
+                for (int r = threadIdx.x; r < Kr; r += NT) len[r] = (int)(x[r] - a[r]);
+                __syncthreads();
             }
-            sb.st(i, src.ld(a[lo] + (i - off[lo])));
+            int64_t mine = 0;
+            for (int r = r0; r < r0 + per && r < Kr; r++) mine += len[r];
+            int64_t tot;
+            int64_t ex = block_exscan<NT>(mine, &tot);
+            for (int r = r0; r < r0 + per && r < Kr; r++) {
+                off[r] = (int)ex;
+                ex += len[r];
+            }
+            if (threadIdx.x == 0) off[Kr] = (int)take;
+            __syncthreads();
+            // one warp per run: coalesced copies of the pieces into shared memory
+            const int lane = threadIdx.x & 31;
+            for (int r = threadIdx.x >> 5; r < Kr; r += NT / 32) {
+                const int64_t s0 = a[r];
+                const int n_r = len[r], o = off[r];
+                for (int i = lane; i < n_r; i += 32) cp_elem(sb, o + i, src, s0 + i);
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
+            for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
+            out += take;
+            M -= take;
+            if constexpr (BIG) {
+                for (int r = threadIdx.x; r < Kr; r += NT) a[r] = x[r];
+                __syncthreads();
+            }
         }
-        __syncthreads();
-        merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
-        for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
-        out += take;
-        M -= take;
-        for (int r = threadIdx.x; r < Kr; r += NT) a[r] = x[r];
-        __syncthreads();
     }
 }
 

@@ -3,26 +3,29 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 
 #include "psort_internal.h"
 #include "psort_kernels.cuh"
 
 namespace ps {
 
-// Threads per CTA (NT) and keys per thread (E) of the tile sort and merge
-// kernels; PNT*PE is the sample-pool size.
+// Threads per CTA and keys per thread of the tile sort (TNT, TE), of the
+// chunk merge (MNT, ME; MNT*ME is the chunk capacity) and of the sample pool
+// (PNT, PE; PNT*PE samples).
 template <typename K> struct Cfg;
 template <> struct Cfg<uint32_t> {
-    static constexpr int NT = 512, E = 16, PNT = 512, PE = 16;
+    static constexpr int TNT = 512, TE = 16, MNT = 1024, ME = 16, PNT = 512, PE = 16;
 };
 template <> struct Cfg<uint64_t> {
-    static constexpr int NT = 512, E = 16, PNT = 512, PE = 16;
+    static constexpr int TNT = 512, TE = 16, MNT = 512, ME = 16, PNT = 512, PE = 16;
 };
 template <> struct Cfg<Rec> {
-    static constexpr int NT = 512, E = 8, PNT = 512, PE = 8;
+    static constexpr int TNT = 512, TE = 8, MNT = 1024, ME = 8, PNT = 512, PE = 8;
 };
 
-constexpr int64_t FMAX = 512;  // largest fan-in of one in-block merge pass
+constexpr int64_t FMAX = 256;  // largest fan-in of one in-block merge pass
+constexpr int MAXLEV = 6;     // refinement levels of one merge job
 
 template <typename K> struct GStore {
     static constexpr size_t bytes = sizeof(K);
@@ -33,35 +36,101 @@ template <> struct GStore<Rec> {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Shape of one merge job: fan-in K, refinement levels, the group capacity
+// of every level and each level's target child size.
+struct MergeShape {
+    int K, nlev;
+    int64_t G[MAXLEV + 1];
+    int64_t cnom[MAXLEV];
+    int64_t jcap;
+    size_t bytes;
+    // byte offsets inside the job's workspace
+    size_t o_lo[MAXLEV + 1], o_hi[MAXLEV + 1], o_base[MAXLEV + 1], o_size[MAXLEV + 1], o_ng[MAXLEV + 1];
+    size_t o_choff[MAXLEV], o_chgrp[MAXLEV], o_spl[MAXLEV], o_big;
+};
+
 // Everything the launches need to know about one sort's shape.
 template <typename K> struct Plan {
-    static constexpr int T = Cfg<K>::NT * Cfg<K>::E;  // tile = merge chunk capacity
+    static constexpr int T = Cfg<K>::TNT * Cfg<K>::TE;    // tile
+    static constexpr int CAP = Cfg<K>::MNT * Cfg<K>::ME;  // merge chunk capacity
     static constexpr int POOL = Cfg<K>::PNT * Cfg<K>::PE;
     int64_t N, n_B, n_P, L, R0;
+    int mode;
     int npass;
     int64_t F[16];
-    int64_t G_max, CH_max, CR_max;
+    MergeShape inblock[16], fin;
     // workspace byte offsets
-    size_t o_data, o_split, o_off, o_piv, o_c, o_samp, o_choff, o_chgrp, o_spl, o_cr, total;
+    size_t o_data, o_split, o_off, o_piv, o_c, o_samp, o_merge, total;
 
-    static int64_t cnom() { return T / 2; }
+    // final chunks aim at 85% of the capacity (splitters land within about
+    // 10% of their targets); oversized ones take the slow exact path
+    static int64_t cnom() { return CAP * 85 / 100; }
     static int64_t jcap(int64_t K_) { return std::max<int64_t>(1, (POOL / 2 - K_) / 2); }
-    int64_t ch_ub(int64_t G) const { return N / cnom() + G + 1; }
+    // children per refinement level: the pool takes about max(2K, 96) samples
+    // per child, so J is capped near POOL/max(2K, 96)
+    static int64_t jlevel(int64_t K_)
+    {
+        int64_t ji = POOL / std::max<int64_t>(2 * K_, 96);
+        ji = std::min<int64_t>(64, std::max<int64_t>(2, ji));
+        return std::min(ji, jcap(K_));
+    }
 
-    void make(int64_t n, int64_t nb, int64_t np)
+    MergeShape shape(int K_, int64_t G0, int64_t Mmax) const
+    {
+        MergeShape m{};
+        m.K = K_;
+        m.jcap = jcap(K_);
+        const int64_t jl = jlevel(K_);
+        int64_t need = (Mmax + cnom() - 1) / cnom();
+        m.nlev = 0;
+        if (jl >= 2)
+            for (int64_t x = need; x > 1 && m.nlev < MAXLEV; x = (x + jl - 1) / jl) m.nlev++;
+        m.G[0] = G0;
+        for (int l = 0; l < m.nlev; l++) {
+            int64_t c = cnom();
+            for (int q = 0; q < m.nlev - 1 - l; q++) c *= jl;
+            m.cnom[l] = c;
+            m.G[l + 1] = N / c + m.G[l] + 1;
+        }
+        size_t o = 0;
+        for (int l = 0; l <= m.nlev; l++) {
+            m.o_lo[l] = o;
+            o += align256((size_t)m.G[l] * K_ * 8);
+            m.o_hi[l] = o;
+            o += align256((size_t)m.G[l] * K_ * 8);
+            m.o_base[l] = o;
+            o += align256((size_t)m.G[l] * 8);
+            m.o_size[l] = o;
+            o += align256((size_t)m.G[l] * 8);
+            m.o_ng[l] = o;
+            o += 256;
+        }
+        for (int l = 0; l < m.nlev; l++) {
+            m.o_choff[l] = o;
+            o += align256((size_t)(m.G[l] + 1) * 8);
+            m.o_chgrp[l] = o;
+            o += align256((size_t)m.G[l + 1] * 4);
+            m.o_spl[l] = o;
+            o += align256((size_t)m.G[l + 1] * sizeof(Splitter<K>));
+        }
+        m.o_big = o;  // counter, then the list of oversized groups
+        o += align256((size_t)(m.G[m.nlev] + 1) * 8);
+        m.bytes = o;
+        return m;
+    }
+
+    void make(int64_t n, int64_t nb, int64_t np, int md)
     {
         N = n;
         n_B = nb;
         n_P = np;
+        mode = md;
         L = (N + n_B - 1) / n_B;
         R0 = (L + T - 1) / T;
         npass = 0;
         for (int64_t x = R0; x > 1; x = (x + FMAX - 1) / FMAX) npass++;
-        int64_t R = R0;
-        G_max = n_P;
-        CH_max = ch_ub(n_P);
-        CR_max = CH_max * n_B;
-        int64_t W = T;
+        size_t mbytes = 0;
+        int64_t R = R0, W = T;
         for (int p = 0; p < npass; p++) {
             int rem = npass - p;
             int64_t f = 2;  // smallest fan-in with f^rem >= R
@@ -72,15 +141,16 @@ template <typename K> struct Plan {
                 f++;
             }
             F[p] = std::min<int64_t>(f, R);
-            int64_t Rp = (L + W - 1) / W;
-            int64_t gpb = (Rp + F[p] - 1) / F[p];
-            int64_t G = n_B * gpb;
-            G_max = std::max(G_max, G);
-            CH_max = std::max(CH_max, ch_ub(G));
-            CR_max = std::max(CR_max, ch_ub(G) * F[p]);
+            const int64_t Rp = (L + W - 1) / W;
+            const int64_t gpb = (Rp + F[p] - 1) / F[p];
+            inblock[p] = shape((int)F[p], n_B * gpb, std::min<int64_t>(F[p] * W, L));
+            mbytes = std::max(mbytes, inblock[p].bytes);
             R = (R + F[p] - 1) / F[p];
             W *= F[p];
         }
+        const int64_t mmax = mode == PS_PIVOT_EXACT ? (N + n_P - 1) / n_P + 1 : N;
+        fin = shape((int)n_B, n_P, mmax);
+        mbytes = std::max(mbytes, fin.bytes);
         size_t o = 0;
         o_data = o;
         o += align256((size_t)N * GStore<K>::bytes + 256);
@@ -94,14 +164,8 @@ template <typename K> struct Plan {
         o += align256((size_t)n_P * 8);
         o_samp = o;
         o += align256((size_t)n_B * std::max<int64_t>(n_P - 1, 1) * GStore<K>::bytes + 256);
-        o_choff = o;
-        o += align256((size_t)(G_max + 1) * 8);
-        o_chgrp = o;
-        o += align256((size_t)CH_max * 4);
-        o_spl = o;
-        o += align256((size_t)CH_max * sizeof(Splitter<K>));
-        o_cr = o;
-        o += align256((size_t)CR_max * 8);
+        o_merge = o;
+        o += mbytes;
         total = o;
     }
 };
@@ -140,59 +204,93 @@ static inline int xf_of(int dtype)
 
 template <typename K> struct Pipeline {
     using C = Cfg<K>;
-    static constexpr int NT = C::NT, E = C::E, PNT = C::PNT, PE = C::PE;
-    static constexpr int T = NT * E, POOL = PNT * PE;
+    static constexpr int TNT = C::TNT, TE = C::TE, MNT = C::MNT, ME = C::ME, PNT = C::PNT, PE = C::PE;
+    static constexpr int T = TNT * TE, CAP = MNT * ME, POOL = PNT * PE;
 
-    static size_t pool_smem(int Kr) { return STagged<K>::bytes(POOL) + 8 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
-    static size_t merge_smem(int Kr) { return SBuf<K>::bytes(T) + 24 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
-    static size_t tile_smem() { return SBuf<K>::bytes(T) + 4 * (size_t)(NT + 1) + 64; }
+    static size_t pool_smem(int Kr) { return STagged<K>::bytes(POOL) + 4 * (size_t)(Kr + 1) + 64; }
+    static constexpr int BE = ME / 2;  // keys per thread of the oversized-group path
+    static size_t merge_smem(int Kr) { return SBuf<K>::bytes(CAP) + 16 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
+    static size_t big_smem(int Kr) { return SBuf<K>::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
+    static size_t tile_smem() { return SBuf<K>::bytes(T) + 64; }
 
     template <int XF>
     static cudaError_t tile_sort(GBuf<K> src, GBuf<K> dst, const Plan<K>& pl, cudaStream_t s)
     {
-        auto f = k_tile_sort<NT, E, K, XF>;
+        auto f = k_tile_sort<TNT, TE, K, XF>;
         cudaError_t e = smem_attr(f, tile_smem());
         if (e != cudaSuccess) return e;
         const int64_t grid = pl.n_B * pl.R0;
         ProfScope ps_("tile_sort", s);
-        f<<<(unsigned)grid, NT, tile_smem(), s>>>(src, dst, pl.N, pl.L, pl.R0);
+        f<<<(unsigned)grid, TNT, tile_smem(), s>>>(src, dst, pl.N, pl.L, pl.R0);
         return cudaGetLastError();
     }
 
-    // Multiway merge of every group of `job` from src into dst.
+    // Multiway merge of every group of `job` from src into dst: level-0 windows,
+    // sh.nlev refinement levels (sample pool, co-ranks, child windows), then
+    // one CTA per final group.
     template <int XF>
-    static cudaError_t merge(const MergeJob& job, int64_t G, GBuf<K> src, GBuf<K> dst, const Plan<K>& pl,
-                             char* ws, cudaStream_t s)
+    static cudaError_t merge(const MergeJob& job, const MergeShape& sh, GBuf<K> src, GBuf<K> dst,
+                             const Plan<K>& pl, char* ws, cudaStream_t s)
     {
         const bool fin = job.kind == 1;
-        int64_t* choff = (int64_t*)(ws + pl.o_choff);
-        int* chgrp = (int*)(ws + pl.o_chgrp);
-        Splitter<K>* spl = (Splitter<K>*)(ws + pl.o_spl);
-        int64_t* cr = (int64_t*)(ws + pl.o_cr);
-        const int64_t* nch = choff + G;
-        const int64_t chub = pl.ch_ub(G);
+        char* m = ws + pl.o_merge;
+        const int Kr = sh.K;
+        Level Lv[MAXLEV + 1];
+        for (int l = 0; l <= sh.nlev; l++) {
+            Lv[l].K = Kr;
+            Lv[l].lo = (int64_t*)(m + sh.o_lo[l]);
+            Lv[l].hi = (int64_t*)(m + sh.o_hi[l]);
+            Lv[l].base = (int64_t*)(m + sh.o_base[l]);
+            Lv[l].size = (int64_t*)(m + sh.o_size[l]);
+            Lv[l].ng = (int64_t*)(m + sh.o_ng[l]);
+        }
+        cudaError_t e;
         {
-            ProfScope ps_(fin ? "chunk_plan_final" : "chunk_plan_inblock", s);
-            k_chunk_plan<1024><<<1, 1024, 0, s>>>(job, G, Plan<K>::cnom(), Plan<K>::jcap(job.K), choff);
+            ProfScope ps_(fin ? "windows_final" : "windows_inblock", s);
+            const int64_t nt = sh.G[0] * Kr;
+            k_root_windows<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(job, sh.G[0], Lv[0]);
         }
         auto fp = k_pool<PNT, PE, K>;
-        cudaError_t e = smem_attr(fp, pool_smem(job.K));
-        if (e != cudaSuccess) return e;
-        {
-            ProfScope ps_(fin ? "pool_final" : "pool_inblock", s);
-            fp<<<(unsigned)G, PNT, pool_smem(job.K), s>>>(job, src, choff, chgrp, spl);
+        if ((e = smem_attr(fp, pool_smem(Kr))) != cudaSuccess) return e;
+        for (int l = 0; l < sh.nlev; l++) {
+            int64_t* choff = (int64_t*)(m + sh.o_choff[l]);
+            int* chgrp = (int*)(m + sh.o_chgrp[l]);
+            Splitter<K>* spl = (Splitter<K>*)(m + sh.o_spl[l]);
+            {
+                ProfScope ps_(fin ? "plan_final" : "plan_inblock", s);
+                k_chunk_plan<1024><<<1, 1024, 0, s>>>(Lv[l], sh.cnom[l], sh.jcap, choff);
+            }
+            {
+                ProfScope ps_(fin ? "pool_final" : "pool_inblock", s);
+                fp<<<(unsigned)sh.G[l], PNT, pool_smem(Kr), s>>>(Lv[l], src, choff, chgrp, spl);
+            }
+            {
+                ProfScope ps_(fin ? "corank_final" : "corank_inblock", s);
+                const int64_t nt = sh.G[l + 1] * Kr;
+                k_corank<K><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(Lv[l], src, spl, choff, chgrp, Lv[l + 1]);
+            }
+            {
+                ProfScope ps_(fin ? "children_final" : "children_inblock", s);
+                k_child_stats<128><<<(unsigned)sh.G[l + 1], 128, 0, s>>>(Lv[l], choff, chgrp, Lv[l + 1]);
+            }
         }
-        const int64_t nthr = chub * job.K;
-        {
-            ProfScope ps_(fin ? "corank_final" : "corank_inblock", s);
-            k_corank<K><<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(job, src, spl, choff, chgrp, nch, cr);
-        }
-        auto fm = k_merge<NT, E, K, XF>;
-        e = smem_attr(fm, merge_smem(job.K));
-        if (e != cudaSuccess) return e;
+        int64_t* big = (int64_t*)(m + sh.o_big);
+        unsigned long long* nbig = (unsigned long long*)big;
+        if ((e = cudaMemsetAsync(nbig, 0, 8, s)) != cudaSuccess) return e;
+        const Level& Lf = Lv[sh.nlev];
+        const int64_t gf = sh.G[sh.nlev];
+        auto fm = k_merge<MNT, ME, K, XF, false>;
+        if ((e = smem_attr(fm, merge_smem(Kr))) != cudaSuccess) return e;
         {
             ProfScope ps_(fin ? "merge_final" : "merge_inblock", s);
-            fm<<<(unsigned)chub, NT, merge_smem(job.K), s>>>(job, src, dst, cr, choff, chgrp, nch);
+            fm<<<(unsigned)gf, MNT, merge_smem(Kr), s>>>(Lf, src, dst, pl.N, big + 1, nbig);
+        }
+        auto fb = k_merge<MNT, BE, K, XF, true>;
+        if ((e = smem_attr(fb, big_smem(Kr))) != cudaSuccess) return e;
+        {
+            ProfScope ps_(fin ? "merge_big_final" : "merge_big_inblock", s);
+            fb<<<(unsigned)std::min<int64_t>(gf, 2 * 152), MNT, big_smem(Kr), s>>>(Lf, src, dst, pl.N, big + 1,
+                                                                                    nbig);
         }
         return cudaGetLastError();
     }
@@ -208,7 +306,7 @@ template <typename K> struct Pipeline {
         if ((e = tile_sort<XF>(user, cur, pl, s)) != cudaSuccess) return e;
         int64_t W = T;
         for (int p = 0; p < pl.npass; p++) {
-            MergeJob job{};
+            MergeJob job{};  // in-block pass p
             job.kind = 0;
             job.K = (int)pl.F[p];
             job.N = pl.N;
@@ -217,7 +315,7 @@ template <typename K> struct Pipeline {
             int64_t Rp = (pl.L + W - 1) / W;
             job.gpb = (Rp + pl.F[p] - 1) / pl.F[p];
             GBuf<K> nxt = same_buf(cur, wsb) ? user : wsb;
-            if ((e = merge<0>(job, pl.n_B * job.gpb, cur, nxt, pl, ws, s)) != cudaSuccess) return e;
+            if ((e = merge<0>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) return e;
             cur = nxt;
             W *= pl.F[p];
         }
@@ -271,7 +369,7 @@ template <typename K> struct Pipeline {
         job.splits = splits;
         job.offsets = offs;
         job.n_P = pl.n_P;
-        if ((e = merge<XF>(job, pl.n_P, cur, user, pl, ws, s)) != cudaSuccess) return e;
+        if ((e = merge<XF>(job, pl.fin, cur, user, pl, ws, s)) != cudaSuccess) return e;
         // Trace.
         if (a.trace) {
             const ps_trace* t = a.trace;
@@ -304,7 +402,7 @@ template <typename K> struct Pipeline {
     static int run(const SortArgs& a)
     {
         Plan<K> pl;
-        pl.make(a.n, a.n_B, a.n_P);
+        pl.make(a.n, a.n_B, a.n_P, a.mode);
         char* ws = nullptr;
         int rc = ws_alloc((void**)&ws, pl.total, a.stream);
         if (rc != PS_OK) return rc;
@@ -322,7 +420,7 @@ template <typename K> struct Pipeline {
     static size_t ws_bytes(int64_t n, int64_t nb, int64_t np)
     {
         Plan<K> pl;
-        pl.make(n, nb, np);
+        pl.make(n, nb, np, PS_PIVOT_REGULAR);
         return pl.total;
     }
 };

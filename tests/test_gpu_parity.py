@@ -131,6 +131,10 @@ CASES = [
     (1_000_003, "float32", "uniform", 4, 200), (1_000_003, "int64", "few_unique", 100, 3),
     (77, "int32", "uniform", 100, 9), (500, "int64", "uniform", 3, 700),
     (2_500_000, "int32", "uniform", 1, 16), (12_345, "float64", "few_unique", 4096, 2),
+    # multi-level refinement of one huge group, and groups too wide to split
+    # (4096 runs) that take the exact sub-chunk path
+    (3_000_000, "int64", "uniform", 2, 1), (300_000, "int64", "uniform", 4096, 3),
+    (1_500_000, "float32", "few_unique", 3, 2),
 ]
 
 
