@@ -136,6 +136,31 @@ const char* ps_status_string(int status);
  * none). */
 int ps_last_cuda_error(void);
 
+/* ---- allocation-free variant -------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: code running while a CUDA graph is
+ * being captured by someone else, real-time loops that forbid allocator
+ * calls, and hosts whose memory pools are owned and capped by another
+ * runtime.  ps_sort_noalloc sorts like ps_sort (same dtypes, pivot modes and
+ * automatic parameters, result bit-identical) but takes all of its workspace
+ * from one static device array of PS_NOALLOC_SCRATCH_BYTES that the library
+ * reserves on every GPU it is loaded on, for the life of the process.
+ *   - n above PS_NOALLOC_MAX_KEYS (or a shape whose workspace would not fit
+ *     the array) is rejected with PS_ERR_INVALID_ARG before any work is queued.
+ *   - It calls no cudaMalloc, cudaFree or pool allocation.  (Keep profiling
+ *     off: ps_profile_enable makes every launch create CUDA events.)
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     outside any stream capture.
+ *   - All calls on a device share the one array and the kernels overwrite
+ *     whatever a previous call left there (the counters they need are zeroed
+ *     on the stream before use).  Two calls whose work overlaps on the GPU --
+ *     on different streams, or from different threads without ordering --
+ *     race on the array and corrupt each other's results: serialise them. */
+#define PS_NOALLOC_MAX_KEYS ((int64_t)1 << 20)
+#define PS_NOALLOC_SCRATCH_BYTES ((size_t)12 << 20)
+int ps_sort_noalloc(void* keys, int64_t n, int dtype, int pivot_mode, ps_stream_t stream);
+
 /* ---- profiling (library-wide, off by default) ---------------------------
  * While enabled, every kernel the library launches is bracketed by two CUDA
  * events recorded on the launch stream, so that per-kernel device time can be

@@ -18,7 +18,7 @@ from ._lib import PS_PIVOT_EXACT, PS_PIVOT_REGULAR, PsortError  # noqa: F401
 
 __all__ = ["sort", "sort_pairs", "sort_host", "resolve_params", "workspace_bytes", "Trace",
            "PsortError", "PS_PIVOT_EXACT", "PS_PIVOT_REGULAR", "profile_enable", "profile_read",
-           "profile_reset"]
+           "profile_reset", "sort_noalloc"]
 
 _MODES = {"regular": _lib.PS_PIVOT_REGULAR, "psrs": _lib.PS_PIVOT_REGULAR, 0: 0,
           "exact": _lib.PS_PIVOT_EXACT, "pses": _lib.PS_PIVOT_EXACT, 1: 1}
@@ -191,3 +191,17 @@ def profile_read() -> dict:
     n = ctypes.c_int()
     _lib.check(lib, "ps_profile_read", lib.ps_profile_read(buf, cap, ctypes.byref(n)))
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n.value, cap))}
+
+
+def sort_noalloc(keys, pivot_mode="exact", stream=None) -> None:
+    """Sort in place through ps_sort_noalloc, the entry point that takes its
+    workspace from the library's static device array instead of allocating
+    (for callers that may not allocate device memory; at most
+    PS_NOALLOC_MAX_KEYS keys, and concurrent calls must be serialised)."""
+    lib = _lib.load()
+    if not keys.is_cuda or keys.dim() != 1 or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous 1-D CUDA tensor")
+    n = keys.numel()
+    rc = lib.ps_sort_noalloc(keys.data_ptr() if n else None, n, _dtype_code(keys.dtype),
+                             _mode(pivot_mode), _stream_handle(stream))
+    _lib.check(lib, "ps_sort_noalloc", rc)

@@ -21,7 +21,9 @@ PS_PIVOT_REGULAR, PS_PIVOT_EXACT = 0, 1
 # every symbol include/psort.h declares
 EXPORTS = ["ps_sort", "ps_sort_ex", "ps_sort_pairs", "ps_sort_host", "ps_resolve_params",
            "ps_workspace_bytes", "ps_status_string", "ps_last_cuda_error", "ps_profile_enable",
-           "ps_profile_read", "ps_profile_reset"]
+           "ps_profile_read", "ps_profile_reset", "ps_sort_noalloc"]
+
+PS_NOALLOC_MAX_KEYS = 1 << 20
 
 
 class PsParams(ctypes.Structure):
@@ -76,12 +78,13 @@ def load(path: str | None = None):
     lib.ps_status_string.argtypes = [i32]
     lib.ps_status_string.restype = ctypes.c_char_p
     lib.ps_last_cuda_error.argtypes = []
+    lib.ps_sort_noalloc.argtypes = [vp, i64, i32, i32, vp]
     lib.ps_profile_enable.argtypes = [i32]
     lib.ps_profile_read.argtypes = [ctypes.POINTER(PsKernelStat), i32, ctypes.POINTER(i32)]
     lib.ps_profile_reset.argtypes = []
     for name in ("ps_sort", "ps_sort_ex", "ps_sort_pairs", "ps_sort_host", "ps_resolve_params",
                  "ps_workspace_bytes", "ps_last_cuda_error", "ps_profile_enable", "ps_profile_read",
-                 "ps_profile_reset"):
+                 "ps_profile_reset", "ps_sort_noalloc"):
         getattr(lib, name).restype = i32
     if path is None:
         _lib = lib

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpsort.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["psort_u32.cu", "psort_u64.cu", "psort_rec.cu", "psort_api.cu"]
+SOURCES = ["psort_u32.cu", "psort_u64.cu", "psort_rec.cu", "psort_api.cu", "psort_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

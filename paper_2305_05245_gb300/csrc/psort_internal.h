@@ -49,5 +49,8 @@ int run_sort_rec(const SortArgs& a);
 size_t ws_bytes_u32(int64_t n, int64_t n_B, int64_t n_P);
 size_t ws_bytes_u64(int64_t n, int64_t n_B, int64_t n_P);
 size_t ws_bytes_rec(int64_t n, int64_t n_B, int64_t n_P);
+// The same sorts on a caller-provided workspace (allocation-free entry point).
+int run_sort_u32_on(const SortArgs& a, char* ws, size_t cap);
+int run_sort_u64_on(const SortArgs& a, char* ws, size_t cap);
 
 }  // namespace ps

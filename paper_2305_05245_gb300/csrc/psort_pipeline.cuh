@@ -417,6 +417,23 @@ template <typename K> struct Pipeline {
         return PS_OK;
     }
 
+    // The same pipeline on a workspace the caller provides (cap bytes at ws);
+    // allocates nothing.  PS_ERR_INVALID_ARG if the plan does not fit.
+    static int run_on(const SortArgs& a, char* ws, size_t cap)
+    {
+        Plan<K> pl;
+        pl.make(a.n, a.n_B, a.n_P, a.mode);
+        if (pl.total > cap) return PS_ERR_INVALID_ARG;
+        cudaError_t e;
+        switch (xf_of(a.dtype)) {
+        case 1: e = run_xf<1>(a, pl, ws); break;
+        case 2: e = run_xf<2>(a, pl, ws); break;
+        default: e = run_xf<0>(a, pl, ws); break;
+        }
+        if (e != cudaSuccess) return fail_cuda(e);
+        return PS_OK;
+    }
+
     static size_t ws_bytes(int64_t n, int64_t nb, int64_t np)
     {
         Plan<K> pl;
