@@ -161,6 +161,15 @@ int ps_last_cuda_error(void);
 #define PS_NOALLOC_SCRATCH_BYTES ((size_t)12 << 20)
 int ps_sort_noalloc(void* keys, int64_t n, int dtype, int pivot_mode, ps_stream_t stream);
 
+/* ---- checked builds -------------------------------------------------------
+ * A build compiled with -DPS_CHECKED (libpsort_checked.so) validates every
+ * global and shared-memory index in its kernels; the first out-of-range
+ * access is not performed but recorded.  ps_debug_violation waits for
+ * nothing, reads and clears that record: it returns 1 and fills out[0..3]
+ * with (site + 100 * key family, index, bound, CTA) if a violation was seen,
+ * 0 if none (always 0 in an ordinary build), or a negative status. */
+int ps_debug_violation(uint64_t* out);
+
 /* ---- profiling (library-wide, off by default) ---------------------------
  * While enabled, every kernel the library launches is bracketed by two CUDA
  * events recorded on the launch stream, so that per-kernel device time can be

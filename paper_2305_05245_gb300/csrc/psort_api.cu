@@ -296,6 +296,28 @@ const char* ps_status_string(int status)
 
 int ps_last_cuda_error(void) { return g_last_cuda; }
 
+int ps_debug_violation(uint64_t* out)
+{
+    if (!out) return PS_ERR_INVALID_ARG;
+    unsigned long long v[4];
+    int (*readers[3])(unsigned long long*) = {viol_read_u32, viol_read_u64, viol_read_rec};
+    int found = 0;
+    for (int f = 0; f < 3; f++) {
+        int rc = readers[f](v);
+        if (rc < 0) return rc;
+        if (rc == 1 && !found) {
+            out[0] = v[0] + 100ull * (unsigned long long)f;
+            out[1] = v[1];
+            out[2] = v[2];
+            out[3] = v[3];
+            found = 1;
+        }
+    }
+    if (!found)
+        for (int i = 0; i < 4; i++) out[i] = 0;
+    return found;
+}
+
 int ps_profile_enable(int on) { return g_prof.exchange(on != 0) ? 1 : 0; }
 
 int ps_profile_read(ps_kernel_stat* out, int cap, int* n)

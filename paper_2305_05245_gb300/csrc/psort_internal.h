@@ -49,6 +49,10 @@ int run_sort_rec(const SortArgs& a);
 size_t ws_bytes_u32(int64_t n, int64_t n_B, int64_t n_P);
 size_t ws_bytes_u64(int64_t n, int64_t n_B, int64_t n_P);
 size_t ws_bytes_rec(int64_t n, int64_t n_B, int64_t n_P);
+// Index-violation records of the checked build (one per key family).
+int viol_read_u32(unsigned long long* out);
+int viol_read_u64(unsigned long long* out);
+int viol_read_rec(unsigned long long* out);
 // The same sorts on a caller-provided workspace (allocation-free entry point).
 int run_sort_u32_on(const SortArgs& a, char* ws, size_t cap);
 int run_sort_u64_on(const SortArgs& a, char* ws, size_t cap);

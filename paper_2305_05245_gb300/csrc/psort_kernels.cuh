@@ -25,6 +25,26 @@
 
 namespace ps {
 
+// ----------------------------------------------------------- checked builds
+// With -DPS_CHECKED every global and shared access of the sort validates its
+// index; the first violation (site, index, bound, CTA) is recorded in ps_viol
+// and the access is skipped instead of performed.  Without the flag the
+// checks compile to nothing.
+#ifdef PS_CHECKED
+static __device__ unsigned long long ps_viol[4];
+static __device__ __noinline__ void ps_violation(int site, long long idx, long long bound)
+{
+    if (atomicCAS(&ps_viol[0], 0ull, (unsigned long long)site) == 0ull) {
+        ps_viol[1] = (unsigned long long)idx;
+        ps_viol[2] = (unsigned long long)bound;
+        ps_viol[3] = blockIdx.x;
+    }
+}
+#define PS_IN(i, n, site) (((long long)(i) >= 0 && (long long)(i) < (long long)(n)) ? true : (ps::ps_violation((site), (long long)(i), (long long)(n)), false))
+#else
+#define PS_IN(i, n, site) true
+#endif
+
 // ---------------------------------------------------------------- key types
 
 // A record: 64-bit key and 32-bit payload, ordered by (key, payload).
@@ -100,25 +120,34 @@ template <int XF> __device__ __forceinline__ uint64_t xform(uint64_t x) { return
 template <typename K> struct GBuf;
 template <> struct GBuf<uint32_t> {
     uint32_t* p;
-    __device__ uint32_t ld(int64_t i) const { return p[i]; }
-    __device__ void st(int64_t i, uint32_t v) const { p[i] = v; }
-    template <int XF> __device__ uint32_t ldx(int64_t i) const { return kappa<XF>(p[i]); }
-    template <int XF> __device__ void stx(int64_t i, uint32_t v) const { p[i] = kappa_inv<XF>(v); }
+    int64_t n;  // element count (checked builds only)
+    __device__ uint32_t ld(int64_t i) const { return PS_IN(i, n, 1) ? p[i] : 0u; }
+    __device__ void st(int64_t i, uint32_t v) const { if (PS_IN(i, n, 2)) p[i] = v; }
+    template <int XF> __device__ uint32_t ldx(int64_t i) const { return kappa<XF>(ld(i)); }
+    template <int XF> __device__ void stx(int64_t i, uint32_t v) const { st(i, kappa_inv<XF>(v)); }
 };
 template <> struct GBuf<uint64_t> {
     uint64_t* p;
-    __device__ uint64_t ld(int64_t i) const { return p[i]; }
-    __device__ void st(int64_t i, uint64_t v) const { p[i] = v; }
-    template <int XF> __device__ uint64_t ldx(int64_t i) const { return kappa<XF>(p[i]); }
-    template <int XF> __device__ void stx(int64_t i, uint64_t v) const { p[i] = kappa_inv<XF>(v); }
+    int64_t n;
+    __device__ uint64_t ld(int64_t i) const { return PS_IN(i, n, 1) ? p[i] : 0ull; }
+    __device__ void st(int64_t i, uint64_t v) const { if (PS_IN(i, n, 2)) p[i] = v; }
+    template <int XF> __device__ uint64_t ldx(int64_t i) const { return kappa<XF>(ld(i)); }
+    template <int XF> __device__ void stx(int64_t i, uint64_t v) const { st(i, kappa_inv<XF>(v)); }
 };
 template <> struct GBuf<Rec> {
     uint64_t* k;
     uint32_t* p;
-    __device__ Rec ld(int64_t i) const { return Rec{k[i], p[i]}; }
-    __device__ void st(int64_t i, const Rec& v) const { k[i] = v.k; p[i] = v.p; }
-    template <int XF> __device__ Rec ldx(int64_t i) const { return Rec{k[i], p[i]}; }
-    template <int XF> __device__ void stx(int64_t i, const Rec& v) const { k[i] = v.k; p[i] = v.p; }
+    int64_t n;
+    __device__ Rec ld(int64_t i) const { return PS_IN(i, n, 1) ? Rec{k[i], p[i]} : Rec{0ull, 0u}; }
+    __device__ void st(int64_t i, const Rec& v) const
+    {
+        if (PS_IN(i, n, 2)) {
+            k[i] = v.k;
+            p[i] = v.p;
+        }
+    }
+    template <int XF> __device__ Rec ldx(int64_t i) const { return ld(i); }
+    template <int XF> __device__ void stx(int64_t i, const Rec& v) const { st(i, v); }
 };
 
 template <int XF> __device__ __forceinline__ Rec xform(const Rec& x) { return x; }
@@ -129,17 +158,29 @@ template <int XF> __device__ __forceinline__ Rec xform(const Rec& x) { return x;
 template <typename K> struct SBuf;
 template <> struct SBuf<uint32_t> {
     uint32_t* a;
-    __device__ __forceinline__ uint32_t ld(int i) const { return a[i + (i >> 5)]; }
-    __device__ __forceinline__ void st(int i, uint32_t v) const { a[i + (i >> 5)] = v; }
+    int cap;  // physical slots (checked builds only)
+    __device__ __forceinline__ uint32_t ld(int i) const { return PS_IN(i + (i >> 5), cap, 4) ? a[i + (i >> 5)] : 0u; }
+    __device__ __forceinline__ void st(int i, uint32_t v) const { if (PS_IN(i + (i >> 5), cap, 5)) a[i + (i >> 5)] = v; }
     static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / 32 + 1) * 4 + 15) & ~(size_t)15; }
-    static __device__ SBuf carve(char*& sp, int n) { SBuf b{(uint32_t*)sp}; sp += bytes(n); return b; }
+    static __device__ SBuf carve(char*& sp, int n)
+    {
+        SBuf b{(uint32_t*)sp, n + n / 32 + 1};
+        sp += bytes(n);
+        return b;
+    }
 };
 template <> struct SBuf<uint64_t> {
     uint64_t* a;
-    __device__ __forceinline__ uint64_t ld(int i) const { return a[i + (i >> 4)]; }
-    __device__ __forceinline__ void st(int i, uint64_t v) const { a[i + (i >> 4)] = v; }
+    int cap;
+    __device__ __forceinline__ uint64_t ld(int i) const { return PS_IN(i + (i >> 4), cap, 4) ? a[i + (i >> 4)] : 0ull; }
+    __device__ __forceinline__ void st(int i, uint64_t v) const { if (PS_IN(i + (i >> 4), cap, 5)) a[i + (i >> 4)] = v; }
     static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / 16 + 1) * 8 + 15) & ~(size_t)15; }
-    static __device__ SBuf carve(char*& sp, int n) { SBuf b{(uint64_t*)sp}; sp += bytes(n); return b; }
+    static __device__ SBuf carve(char*& sp, int n)
+    {
+        SBuf b{(uint64_t*)sp, n + n / 16 + 1};
+        sp += bytes(n);
+        return b;
+    }
 };
 template <> struct SBuf<Rec> {
     SBuf<uint64_t> k;
@@ -175,16 +216,18 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 __device__ __forceinline__ void cp_elem(const SBuf<uint32_t>& s, int i, const GBuf<uint32_t>& g, int64_t j)
 {
-    cp_async4(s.a + i + (i >> 5), g.p + j);
+    if (PS_IN(i + (i >> 5), s.cap, 6) && PS_IN(j, g.n, 3)) cp_async4(s.a + i + (i >> 5), g.p + j);
 }
 __device__ __forceinline__ void cp_elem(const SBuf<uint64_t>& s, int i, const GBuf<uint64_t>& g, int64_t j)
 {
-    cp_async8(s.a + i + (i >> 4), g.p + j);
+    if (PS_IN(i + (i >> 4), s.cap, 6) && PS_IN(j, g.n, 3)) cp_async8(s.a + i + (i >> 4), g.p + j);
 }
 __device__ __forceinline__ void cp_elem(const SBuf<Rec>& s, int i, const GBuf<Rec>& g, int64_t j)
 {
-    cp_async8(s.k.a + i + (i >> 4), g.k + j);
-    cp_async4(s.p.a + i + (i >> 5), g.p + j);
+    if (PS_IN(i + (i >> 4), s.k.cap, 6) && PS_IN(j, g.n, 3)) {
+        cp_async8(s.k.a + i + (i >> 4), g.k + j);
+        cp_async4(s.p.a + i + (i >> 5), g.p + j);
+    }
 }
 
 // Storage views used by the merge routine: plain keys, or keys carrying a
@@ -559,6 +602,7 @@ struct MergeJob {
 // of the destination; *ng groups exist (a device-side count).
 struct Level {
     int K;
+    int64_t cap;  // group capacity of the tables (checked builds validate against it)
     int64_t* lo;
     int64_t* hi;
     int64_t* base;
@@ -577,6 +621,7 @@ __global__ void k_root_windows(MergeJob job, int64_t G, Level L)
     int64_t lo, hi;
     job.run(g, r, lo, hi);
     if (hi < lo) hi = lo;
+    if (!PS_IN(g, L.cap, 20)) return;
     L.lo[idx] = lo;
     L.hi[idx] = hi;
     if (r == 0) {
@@ -600,7 +645,8 @@ __device__ __forceinline__ int64_t chunks_for(int64_t M, int64_t cnom, int64_t j
 template <int NT>
 __global__ void __launch_bounds__(NT) k_chunk_plan(Level L, int64_t cnom, int64_t jcap, int64_t* choff)
 {
-    const int64_t G = *L.ng;
+    const int64_t G = *L.ng < L.cap ? *L.ng : L.cap;
+    PS_IN(*L.ng, L.cap + 1, 21);
     int64_t carry = 0;
     for (int64_t base = 0; base < G; base += NT) {
         const int64_t g = base + threadIdx.x;
@@ -629,16 +675,25 @@ template <typename K> struct Splitter {
 // it (inclusive) and child j starts after it.
 template <int NT, int E, typename K>
 __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t* choff, int* chgrp,
-                                             Splitter<K>* spl)
+                                             Splitter<K>* spl, int64_t ccap)
 {
     constexpr int POOL = NT * E;
     extern __shared__ __align__(16) char smem[];
     const int64_t g = blockIdx.x;
-    if (g >= *L.ng) return;
+    const int64_t ng = *L.ng < L.cap ? *L.ng : L.cap;
+    if (g >= ng) return;
     const int64_t c0 = choff[g];
     const int64_t J = choff[g + 1] - c0;
-    for (int64_t j = threadIdx.x; j < J; j += NT) chgrp[c0 + j] = (int)g;
+    if (!PS_IN(c0 + J - 1, ccap, 22) || c0 < 0 || J < 1 || c0 + J > ccap) return;
+    // every slot first holds a splitter above all keys, so that a slot the
+    // assignment below could miss yields an empty child (and an oversized
+    // sibling, merged exactly) rather than stale bytes
+    for (int64_t j = threadIdx.x; j < J; j += NT) {
+        chgrp[c0 + j] = (int)g;
+        spl[c0 + j] = Splitter<K>{KT<K>::maxkey(), 0xFFFFFFFFu, 0xFFFFFFFFu};
+    }
     if (J <= 1) return;
+    __syncthreads();
     const int Kr = L.K;
     const int64_t* lo = L.lo + g * Kr;
     const int64_t* hi = L.hi + g * Kr;
@@ -666,6 +721,7 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
     if (threadIdx.x == 0) off[Kr] = (int)P64;
     __syncthreads();
     const int P = (int)P64;  // <= M/S + K <= POOL
+    if (!PS_IN(P, POOL + 1, 23) || P > POOL) return;
     for (int i = threadIdx.x; i < P; i += NT) {
         int x = 0, y = Kr - 1;  // run holding pool slot i: last r with off[r] <= i
         while (x < y) {
@@ -676,6 +732,7 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
         int64_t q = (int64_t)(i - off[x]) * S + (S - 1);
         const int64_t last = hi[x] - lo[x] - 1;
         if (q > last) q = last;
+        if (!PS_IN(q, last + 1, 24)) continue;
         cp_elem(pool.kb, i, src, lo[x] + q);
         pool.tb.st(i, ((uint64_t)x << 32) | (uint64_t)q);
     }
@@ -690,6 +747,7 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
         if (q0 + i < P) {
             const uint64_t tag = pool.tb.ld(q0 + i);
             const int x = (int)(tag >> 32);
+            if (!PS_IN(x, Kr, 25)) continue;
             const int64_t q = (int64_t)(uint32_t)tag, len = hi[x] - lo[x];
             wsum += (q == len - 1 && len % S) ? len % S : S;
         }
@@ -704,11 +762,17 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
         if (q0 + i < P) {
             const Tagged<K> e = pool.ld(q0 + i);
             const int x = (int)(e.tag >> 32);
+            if (!PS_IN(x, Kr, 26)) continue;
             const int64_t q = (int64_t)(uint32_t)e.tag, len = hi[x] - lo[x];
             const int64_t ci = cb + ((q == len - 1 && len % S) ? len % S : S);
-            // splitters j whose target max(1, floor(j*M/J) - adj) lies in (cb, ci]
-            int64_t j = (int64_t)(((unsigned __int128)(cb + adj) * (uint64_t)J) / (uint64_t)M) - 1;
-            if (j < 1) j = 1;
+            // splitters j whose target t_j = max(1, floor(j*M/J) - adj) lies in
+            // (cb, ci]; for cb >= 1 only unclamped targets qualify, and those
+            // satisfy j >= (cb + adj + 1) * J / M
+            int64_t j = 1;
+            if (cb > 0) {
+                j = (int64_t)(((unsigned __int128)(cb + adj + 1) * (uint64_t)J) / (uint64_t)M) - 1;
+                if (j < 1) j = 1;
+            }
             for (; j < J; j++) {
                 int64_t t = (int64_t)(((unsigned __int128)j * (uint64_t)M) / (uint64_t)J) - adj;
                 if (t < 1) t = 1;
@@ -732,8 +796,11 @@ __global__ void k_corank(Level L, GBuf<K> src, const Splitter<K>* spl, const int
     const int Kr = L.K;
     const int64_t c = idx / Kr;
     const int r = (int)(idx - c * Kr);
-    if (c >= choff[*L.ng]) return;
+    const int64_t ng = *L.ng < L.cap ? *L.ng : L.cap;
+    if (c >= choff[ng]) return;
+    if (!PS_IN(c, C.cap, 27) || c >= C.cap) return;
     const int64_t g = chgrp[c];
+    if (!PS_IN(g, ng, 28) || g < 0 || g >= ng) return;
     const int64_t lo = L.lo[g * Kr + r], hi = L.hi[g * Kr + r];
     int64_t v;
     if (c == choff[g]) {
@@ -754,15 +821,20 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* choff, const int* chgrp, Level C)
 {
     const int64_t c = blockIdx.x;
-    const int64_t nch = choff[*L.ng];
+    const int64_t ng = *L.ng < L.cap ? *L.ng : L.cap;
+    int64_t nch = choff[ng];
+    PS_IN(nch, C.cap + 1, 29);
+    if (nch > C.cap) nch = C.cap;
     if (c >= nch) return;
     const int Kr = L.K;
     const int64_t g = chgrp[c];
+    if (!PS_IN(g, ng, 30) || g < 0 || g >= ng) return;
     const bool last = c + 1 >= choff[g + 1];
     int64_t before = 0, sz = 0;
     for (int r = threadIdx.x; r < Kr; r += NT) {
         const int64_t lo = C.lo[c * Kr + r];
         int64_t hi = last ? L.hi[g * Kr + r] : C.lo[(c + 1) * Kr + r];
+        PS_IN(hi - lo, INT64_MAX, 34);  // siblings' windows must not run backwards
         if (hi < lo) hi = lo;
         C.hi[c * Kr + r] = hi;
         before += lo - L.lo[g * Kr + r];
@@ -887,15 +959,20 @@ __global__ void __launch_bounds__(NT) k_merge(Level C, GBuf<K> src, GBuf<K> dst,
     int* off = len + Kr;                             // piece offsets in shared memory
     const int per = (Kr + NT - 1) / NT;
     const int r0 = threadIdx.x * per;
-    const int64_t nwork = BIG ? (int64_t)*nbig : *C.ng;
+    int64_t nwork = BIG ? (int64_t)*nbig : *C.ng;
+    if (nwork > C.cap) nwork = C.cap;
     const int64_t stride = BIG ? gridDim.x : (nwork > 0 ? nwork : 1);
     for (int64_t w = blockIdx.x; w < nwork; w += stride) {
         const int64_t c = BIG ? big[w] : w;
+        if (!PS_IN(c, C.cap, 31) || c < 0 || c >= C.cap) continue;
         int64_t out = C.base[c];
         int64_t M = C.size[c];
         if (out < 0 || M < 0 || out + M > nout) continue;  // never write outside the output
         if (!BIG && M > CAP) {
-            if (threadIdx.x == 0) big[atomicAdd(nbig, 1ull)] = c;
+            if (threadIdx.x == 0) {
+                const unsigned long long slot = atomicAdd(nbig, 1ull);
+                if (PS_IN(slot, C.cap, 32) && slot < (unsigned long long)C.cap) big[slot] = c;
+            }
             continue;
         }
         for (int r = threadIdx.x; r < Kr; r += NT) {
@@ -960,6 +1037,7 @@ __global__ void k_psrs_samples(GBuf<K> blk, GBuf<K> samples, int64_t N, int64_t 
     const int64_t bs = b * L, be = bs + L < N ? bs + L : N;
     const int64_t m = be - bs;
     const int64_t pos = (int64_t)(((unsigned __int128)j * (uint64_t)m) / (uint64_t)n_P);
+    if (!PS_IN(pos, m, 33)) return;
     samples.st(idx, blk.ld(bs + pos));
 }
 

@@ -171,17 +171,17 @@ template <typename K> struct Plan {
 };
 
 template <typename K> static GBuf<K> gbuf_at(char* base, int64_t n);
-template <> inline GBuf<uint32_t> gbuf_at<uint32_t>(char* base, int64_t) { return GBuf<uint32_t>{(uint32_t*)base}; }
-template <> inline GBuf<uint64_t> gbuf_at<uint64_t>(char* base, int64_t) { return GBuf<uint64_t>{(uint64_t*)base}; }
+template <> inline GBuf<uint32_t> gbuf_at<uint32_t>(char* base, int64_t n) { return GBuf<uint32_t>{(uint32_t*)base, n}; }
+template <> inline GBuf<uint64_t> gbuf_at<uint64_t>(char* base, int64_t n) { return GBuf<uint64_t>{(uint64_t*)base, n}; }
 template <> inline GBuf<Rec> gbuf_at<Rec>(char* base, int64_t n)
 {
-    return GBuf<Rec>{(uint64_t*)base, (uint32_t*)(base + align256((size_t)n * 8))};
+    return GBuf<Rec>{(uint64_t*)base, (uint32_t*)(base + align256((size_t)n * 8)), n};
 }
 
 template <typename K> static GBuf<K> gbuf_user(const SortArgs& a);
-template <> inline GBuf<uint32_t> gbuf_user<uint32_t>(const SortArgs& a) { return GBuf<uint32_t>{(uint32_t*)a.keys}; }
-template <> inline GBuf<uint64_t> gbuf_user<uint64_t>(const SortArgs& a) { return GBuf<uint64_t>{(uint64_t*)a.keys}; }
-template <> inline GBuf<Rec> gbuf_user<Rec>(const SortArgs& a) { return GBuf<Rec>{(uint64_t*)a.keys, a.payload}; }
+template <> inline GBuf<uint32_t> gbuf_user<uint32_t>(const SortArgs& a) { return GBuf<uint32_t>{(uint32_t*)a.keys, a.n}; }
+template <> inline GBuf<uint64_t> gbuf_user<uint64_t>(const SortArgs& a) { return GBuf<uint64_t>{(uint64_t*)a.keys, a.n}; }
+template <> inline GBuf<Rec> gbuf_user<Rec>(const SortArgs& a) { return GBuf<Rec>{(uint64_t*)a.keys, a.payload, a.n}; }
 
 template <typename K> static bool same_buf(const GBuf<K>& x, const GBuf<K>& y);
 template <> inline bool same_buf<uint32_t>(const GBuf<uint32_t>& x, const GBuf<uint32_t>& y) { return x.p == y.p; }
@@ -238,6 +238,7 @@ template <typename K> struct Pipeline {
         Level Lv[MAXLEV + 1];
         for (int l = 0; l <= sh.nlev; l++) {
             Lv[l].K = Kr;
+            Lv[l].cap = sh.G[l];
             Lv[l].lo = (int64_t*)(m + sh.o_lo[l]);
             Lv[l].hi = (int64_t*)(m + sh.o_hi[l]);
             Lv[l].base = (int64_t*)(m + sh.o_base[l]);
@@ -262,7 +263,7 @@ template <typename K> struct Pipeline {
             }
             {
                 ProfScope ps_(fin ? "pool_final" : "pool_inblock", s);
-                fp<<<(unsigned)sh.G[l], PNT, pool_smem(Kr), s>>>(Lv[l], src, choff, chgrp, spl);
+                fp<<<(unsigned)sh.G[l], PNT, pool_smem(Kr), s>>>(Lv[l], src, choff, chgrp, spl, sh.G[l + 1]);
             }
             {
                 ProfScope ps_(fin ? "corank_final" : "corank_inblock", s);
@@ -442,11 +443,11 @@ template <typename K> struct Pipeline {
     }
 };
 
-template <> inline GBuf<uint32_t> Pipeline<uint32_t>::trace_buf(const ps_trace* t) { return GBuf<uint32_t>{(uint32_t*)t->pivots}; }
-template <> inline GBuf<uint64_t> Pipeline<uint64_t>::trace_buf(const ps_trace* t) { return GBuf<uint64_t>{(uint64_t*)t->pivots}; }
+template <> inline GBuf<uint32_t> Pipeline<uint32_t>::trace_buf(const ps_trace* t) { return GBuf<uint32_t>{(uint32_t*)t->pivots, INT64_MAX}; }
+template <> inline GBuf<uint64_t> Pipeline<uint64_t>::trace_buf(const ps_trace* t) { return GBuf<uint64_t>{(uint64_t*)t->pivots, INT64_MAX}; }
 template <> inline GBuf<Rec> Pipeline<Rec>::trace_buf(const ps_trace* t)
 {
-    return GBuf<Rec>{(uint64_t*)t->pivots, t->pivot_payload};
+    return GBuf<Rec>{(uint64_t*)t->pivots, t->pivot_payload, INT64_MAX};
 }
 
 }  // namespace ps

@@ -118,3 +118,86 @@ def records(n: int, seed: int = 1, dist: str = "uniform"):
     k = keys(n, "uint64", dist, seed)
     p = np.arange(n, dtype=np.uint64).astype(np.uint32)
     return k, p
+
+
+# ----------------------------------------------------------------- device twin
+def _mix_t(z):
+    """SplitMix64 finaliser on int64 torch tensors (two's-complement wrap;
+    logical right shifts emulated with masks)."""
+    import torch
+
+    def shr(x, k):
+        return (x >> k) & ((1 << (64 - k)) - 1)
+
+    m1 = torch.tensor(0xBF58476D1CE4E5B9 - (1 << 64), dtype=torch.int64, device=z.device)
+    m2 = torch.tensor(0x94D049BB133111EB - (1 << 64), dtype=torch.int64, device=z.device)
+    z = (z ^ shr(z, 30)) * m1
+    z = (z ^ shr(z, 27)) * m2
+    return z ^ shr(z, 31)
+
+
+def splitmix64_torch(seed: int, n: int, device="cuda", start: int = 0):
+    """The same stream as splitmix64(), computed on a torch device (int64
+    tensor holding the uint64 bits)."""
+    import torch
+    s = seed & 0xFFFFFFFFFFFFFFFF
+    s = s - (1 << 64) if s >= (1 << 63) else s
+    g = 0x9E3779B97F4A7C15 - (1 << 64)
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    step = 1 << 26
+    for lo in range(0, n, step):
+        hi = min(n, lo + step)
+        i = torch.arange(start + lo + 1, start + hi + 1, dtype=torch.int64, device=device)
+        out[lo:hi] = _mix_t(i * g + s)
+    return out
+
+
+def keys_torch(n: int, dtype: str = "int64", dist: str = "uniform", seed: int = 1, device="cuda"):
+    """Device twin of keys() for the integer dtypes (bit-identical output) and
+    the float uniform/few-unique cases; returns a torch tensor (uint dtypes as
+    same-width signed storage)."""
+    import torch
+    z = splitmix64_torch(seed, n, device)
+    if dist in ("uniform", "sorted", "reverse"):
+        k = _uniform_bits_torch(dtype, z)
+        if dist != "uniform":
+            k = _sort_like_numpy(k, dtype)
+            if dist == "reverse":
+                k = torch.flip(k, [0])
+        return k
+    if dist == "few_unique":
+        vals = _uniform_bits_torch(dtype, splitmix64_torch(seed ^ 0x5A5A5A5A, 16, device))
+        idx = (z >> 60) & 15
+        return vals[idx]
+    if dist == "gaussian":
+        # Box-Muller on the device: the same streams as keys(), but the device's
+        # log/cos may round differently from numpy's in the last place
+        z2 = splitmix64_torch(seed ^ 0xC3C3C3C3C3C3C3C3, n, device)
+        u1 = (((z >> 11) & ((1 << 53) - 1)).to(torch.float64) + 1.0) * (2.0 ** -53)
+        u2 = ((z2 >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+        g = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * torch.pi * u2)
+        return g.to(torch.float32 if dtype == "float32" else torch.float64)
+    raise ValueError("keys_torch supports uniform, sorted, reverse, few_unique and gaussian")
+
+
+def _uniform_bits_torch(dtype, z):
+    import torch
+    if dtype in ("int32", "uint32"):
+        hi = (z >> 32) & 0xFFFFFFFF                      # the upper 32 bits, as 0..2^32-1
+        return (hi - ((hi >> 31) << 32)).to(torch.int32)  # reinterpreted as int32
+    if dtype in ("int64", "uint64"):
+        return z
+    if dtype == "float32":
+        return ((z >> 40) & 0xFFFFFF).to(torch.float32) * (2.0 ** -24)
+    if dtype == "float64":
+        return ((z >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+    raise ValueError(dtype)
+
+
+def _sort_like_numpy(k, dtype):
+    import torch
+    if dtype == "uint32":
+        return k[torch.argsort(k.to(torch.int64) & 0xFFFFFFFF, stable=True)]
+    if dtype == "uint64":
+        return k[torch.argsort(k ^ (-(1 << 63)), stable=True)]
+    return torch.sort(k, stable=True)[0]

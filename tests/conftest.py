@@ -17,3 +17,17 @@ def ora():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(autouse=True)
+def _no_index_violation(request):
+    """With a bounds-checked library (PSORT_LIB=.../libpsort_checked.so) every
+    GPU test also fails if a kernel recorded an out-of-range index."""
+    yield
+    if request.node.get_closest_marker("gpu") is None or "checked" not in os.environ.get("PSORT_LIB", ""):
+        return
+    import ctypes
+    from paper_2305_05245_gb300 import _lib
+    out = (ctypes.c_uint64 * 4)()
+    rc = _lib.load().ps_debug_violation(out)
+    assert rc == 0, "kernel index violation: site %d index %d bound %d cta %d" % tuple(out)
