@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
+    ap.add_argument("--workload", default="single", choices=["single", "batch"])
+    ap.add_argument("--segments", type=int, default=20000)
+    ap.add_argument("--baseline-segments", type=int, default=2000,
+                    help="segments timed with one ps_sort call each (batch workload)")
     return ap.parse_args()
 
 
@@ -173,11 +177,101 @@ def run_reference(a):
     return 0
 
 
+# ------------------------------------------------------------ batched workload
+def batch_shape(n_segs: int, seed: int):
+    """Segment lengths floor(2^U), U ~ Uniform[6, 22] (seeded), as offsets."""
+    import numpy as np
+    import synth
+    z = synth.splitmix64(seed, n_segs)
+    u = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    lens = np.floor(2.0 ** (6.0 + 16.0 * u)).astype(np.int64)
+    offs = np.zeros(n_segs + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    return offs
+
+
+def run_batch(a):
+    """NEXT-1: one ps_sort_batch call over all segments per step, against one
+    ps_sort call per segment (timed on a prefix of the same segments)."""
+    import numpy as np
+    import torch
+
+    import paper_2305_05245_gb300 as ps
+    import synth
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    offs = batch_shape(a.segments, synth.seed_for("batch-shape", a.segments))
+    n = int(offs[-1])
+    pristine = torch.empty(n, dtype=getattr(torch, a.dtype), device=dev)
+    step = 1 << 28
+    for lo in range(0, n, step):
+        hi = min(n, lo + step)
+        pristine[lo:hi] = synth.keys_torch(hi - lo, a.dtype, a.dist, seed=synth.seed_for("batch", lo), device=dev)
+    keys = torch.empty_like(pristine)
+    o_dev = torch.from_numpy(offs).to(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        keys.copy_(pristine)
+        ps.sort_batch(keys, o_dev, a.pivot)
+    torch.cuda.synchronize()
+    ok = True
+    for i in range(0, a.segments, max(1, a.segments // 50)):  # spot checks: segments sorted
+        seg = keys[offs[i]:offs[i + 1]]
+        ok = ok and bool((seg[1:] >= seg[:-1]).all().item())
+    ps.profile_reset()
+    ps.profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    torch.cuda.synchronize()
+    with Clocks(dev.index) as clk:
+        for i in range(a.steps):
+            keys.copy_(pristine)
+            evs[i][0].record(stream)
+            ps.sort_batch(keys, o_dev, a.pivot)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    ps.profile_enable(False)
+    prof = ps.profile_read()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps
+    # the plain path: one ps_sort per segment, on the first baseline-segments segments
+    nb = min(a.baseline_segments, a.segments)
+    keys.copy_(pristine)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(nb):
+        seg = keys[offs[i]:offs[i + 1]]
+        if seg.numel() > 1:
+            ps.sort(seg, a.pivot)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    base_ms = e0.elapsed_time(e1)
+    base_keys = int(offs[nb] - offs[0])
+    line = {
+        "metric": "batched segments/s", "value": a.segments / (ms / 1e3), "unit": "segments/s",
+        "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": a.dtype,
+        "data": "synthetic (SplitMix64, seeded), resident in HBM",
+        "config": {"workload": "batch of %d segments, lengths floor(2^U), U~U[6,22], %s %s, %s splitting"
+                               % (a.segments, a.dtype, a.dist, a.pivot),
+                   "keys": n, "keys_per_s": n / (ms / 1e3)},
+        "per_segment_ps_sort": {"segments": nb, "keys": base_keys, "ms": base_ms,
+                                "value": nb / (base_ms / 1e3), "unit": "segments/s",
+                                "keys_per_s": base_keys / (base_ms / 1e3)},
+        "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in prof.items()},
+        "gpu_launches": sum(v[0] for v in prof.values()),
+        "clocks": clk.summary(), "check": "ok" if ok else "FAILED",
+    }
+    print(json.dumps(line))
+    return 0 if ok else 1
+
+
 # ------------------------------------------------------------ native arm
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batch":
+        return run_batch(a)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -114,6 +114,18 @@ int ps_sort_ex(void* keys, int64_t n, int dtype, int pivot_mode, const ps_params
 int ps_sort_pairs(uint64_t* keys, uint32_t* payload, int64_t n, int pivot_mode,
                   const ps_params* params, const ps_trace* trace, ps_stream_t stream);
 
+/* Sort many independent segments of one key array in place: segment i is
+ * keys[seg_offsets[i], seg_offsets[i+1]) (seg_offsets: n_segs+1 non-decreasing
+ * DEVICE int64 offsets).  Segments are binned by length; every bin runs the
+ * four-step method on all of its segments at once (segments that fit one
+ * shared-memory tile are sorted by one CTA each, in a single launch), so the
+ * number of kernel launches depends on the number of size bins, not on the
+ * number of segments.  Each segment's result equals ps_sort on it alone.
+ * The call reads seg_offsets back to the host (it waits for `stream` once,
+ * before queuing the sort); it returns once the sort is queued. */
+int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dtype, int pivot_mode,
+                  ps_stream_t stream);
+
 /* End-to-end form for callers whose keys live in HOST memory (pinned or
  * pageable): copies the n keys to the device, sorts them as ps_sort_ex does,
  * copies the result back into `host_keys`, and waits for `stream` to finish

@@ -18,7 +18,7 @@ from ._lib import PS_PIVOT_EXACT, PS_PIVOT_REGULAR, PsortError  # noqa: F401
 
 __all__ = ["sort", "sort_pairs", "sort_host", "resolve_params", "workspace_bytes", "Trace",
            "PsortError", "PS_PIVOT_EXACT", "PS_PIVOT_REGULAR", "profile_enable", "profile_read",
-           "profile_reset", "sort_noalloc"]
+           "profile_reset", "sort_noalloc", "sort_batch"]
 
 _MODES = {"regular": _lib.PS_PIVOT_REGULAR, "psrs": _lib.PS_PIVOT_REGULAR, 0: 0,
           "exact": _lib.PS_PIVOT_EXACT, "pses": _lib.PS_PIVOT_EXACT, 1: 1}
@@ -205,3 +205,21 @@ def sort_noalloc(keys, pivot_mode="exact", stream=None) -> None:
     rc = lib.ps_sort_noalloc(keys.data_ptr() if n else None, n, _dtype_code(keys.dtype),
                              _mode(pivot_mode), _stream_handle(stream))
     _lib.check(lib, "ps_sort_noalloc", rc)
+
+
+def sort_batch(keys, seg_offsets, pivot_mode="exact", stream=None) -> None:
+    """Sort every segment keys[seg_offsets[i]:seg_offsets[i+1]] in place with
+    one batched call (ps_sort_batch).  ``seg_offsets`` is an int64 CUDA tensor
+    of n_segs+1 non-decreasing offsets."""
+    lib = _lib.load()
+    if not keys.is_cuda or keys.dim() != 1 or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous 1-D CUDA tensor")
+    import torch
+    if seg_offsets.dtype != torch.int64 or not seg_offsets.is_cuda or not seg_offsets.is_contiguous():
+        raise ValueError("seg_offsets must be a contiguous int64 CUDA tensor")
+    n_segs = seg_offsets.numel() - 1
+    if n_segs < 1:
+        return
+    rc = lib.ps_sort_batch(seg_offsets.data_ptr(), n_segs, keys.data_ptr() if keys.numel() else None,
+                           _dtype_code(keys.dtype), _mode(pivot_mode), _stream_handle(stream))
+    _lib.check(lib, "ps_sort_batch", rc)

@@ -20,6 +20,15 @@ struct SortArgs {
     int64_t n_B, n_P;    // resolved
     const ps_trace* trace;
     cudaStream_t stream;
+    // Batched sorts: n_inst independent instances sharing n_B and n_P, with
+    // device arrays of their starts and lengths.  inst_base == nullptr means
+    // one sort of n keys at offset 0.
+    const int64_t* inst_base = nullptr;
+    const int64_t* inst_n = nullptr;
+    int64_t n_inst = 1;
+    int64_t n_max = 0;   // longest instance
+    int64_t n_sum = 0;   // keys over all instances
+    int64_t extent = 0;  // extent of the key arrays (largest end offset)
 };
 
 // Workspace from the library's stream-ordered pool.

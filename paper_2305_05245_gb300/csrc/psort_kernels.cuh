@@ -507,25 +507,54 @@ __device__ __forceinline__ int64_t bound(const GBuf<K>& src, int64_t lo, int64_t
     return a - lo;
 }
 
+// ------------------------------------------------------------- instances
+// A batch of independent sorts that share n_B and n_P (the batched entry
+// point bins segments by size; a single sort is one instance).  Instance i
+// occupies [off(i), off(i) + len(i)) of the key arrays; its blocks have
+// length ceil(len(i) / n_B).
+struct Inst {
+    const int64_t* base;  // per-instance start (nullptr: one instance at 0)
+    const int64_t* n;     // per-instance length
+    int64_t count;
+    int64_t n0;           // length of the single instance when base is null
+    __device__ __forceinline__ int64_t off(int64_t i) const { return base ? base[i] : 0; }
+    __device__ __forceinline__ int64_t len(int64_t i) const { return base ? n[i] : n0; }
+};
+
+// Bounds [bs, be) of block b (relative to its instance) for instance length N.
+__device__ __forceinline__ void block_bounds(int64_t N, int64_t n_B, int64_t b, int64_t& bs, int64_t& be)
+{
+    const int64_t L = (N + n_B - 1) / n_B;
+    bs = b * L < N ? b * L : N;
+    be = bs + L < N ? bs + L : N;
+}
+
 // ------------------------------------------------------------ step 1: tiles
-// One CTA sorts one tile of NT*E keys of one block (tiles never straddle a
-// block boundary).  Loads apply the order-key transform XF.  The tile is
-// padded with the largest key, which sorts last and is never written.
-template <int NT, int E, typename K, int XF>
-__global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, int64_t N, int64_t L,
-                                                  int64_t tiles_per_block)
+// One CTA sorts one tile of NT*E keys of one block of one instance (tiles
+// never straddle a block boundary; every block gets R0 tile slots, the
+// number the longest block needs).  Loads apply the order-key transform XF.
+// Missing keys of a short tile count as the largest key, which sorts last
+// and is never written.  FINAL: the tile is the whole sorted result, so the
+// store applies the inverse transform.
+template <int NT, int E, typename K, int XF, bool FINAL>
+__global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst in, int64_t n_B, int64_t R0)
 {
     constexpr int T = NT * E;
     extern __shared__ __align__(16) char smem[];
     char* sp = smem;
     SBuf<K> sb = SBuf<K>::carve(sp, T);
-    const int64_t b = blockIdx.x / tiles_per_block, t = blockIdx.x - b * tiles_per_block;
-    const int64_t bs = b * L < N ? b * L : N;
-    const int64_t be = bs + L < N ? bs + L : N;
+    const int64_t per_inst = n_B * R0;
+    const int64_t inst = blockIdx.x / per_inst;
+    const int64_t rest = blockIdx.x - inst * per_inst;
+    const int64_t b = rest / R0, t = rest - b * R0;
+    if (inst >= in.count) return;
+    int64_t bs, be;
+    block_bounds(in.len(inst), n_B, b, bs, be);
     const int64_t ts = bs + t * T;
     if (ts >= be) return;
+    const int64_t o = in.off(inst) + ts;
     const int n = (int)(be - ts < T ? be - ts : T);
-    for (int i = threadIdx.x; i < n; i += NT) cp_elem(sb, i, src, ts + i);
+    for (int i = threadIdx.x; i < n; i += NT) cp_elem(sb, i, src, o + i);
     cp_async_wait_all();
     __syncthreads();
     K r[E];
@@ -539,61 +568,75 @@ __global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, int6
     for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
     __syncthreads();
     merge_levels_pow2<NT, E>(SKeys<K>{sb});
-    for (int i = threadIdx.x; i < n; i += NT) dst.st(ts + i, sb.ld(i));
+    for (int i = threadIdx.x; i < n; i += NT) {
+        if (FINAL) dst.template stx<XF>(o + i, sb.ld(i));
+        else dst.st(o + i, sb.ld(i));
+    }
 }
 
 // ----------------------------------------------------------- merge jobs
 // A merge job is a set of groups; group g merges K sorted runs of `src`
-// into one sorted range of `dst` starting at out_base(g).
-//   kind 0 (in-block pass, step 1): group = (block b, index gi); run r covers
-//          [bs + (gi*K + r)*W, +W) clipped to the block; output in place.
-//   kind 1 (final merge, step 4): group = partition k; run r = block r's
-//          piece [bs + s[r][k], bs + s[r][k+1]); output at O_k.
+// into one sorted range of `dst` starting at out_base(g).  Groups are
+// numbered instance by instance.
+//   kind 0 (in-block pass, step 1): group = (instance, block b, index gi); run
+//          r covers [bs + (gi*K + r)*W, +W) clipped to the block; output in place.
+//   kind 1 (final merge, step 4): group = (instance, partition k); run r =
+//          block r's piece [bs + s[r][k], bs + s[r][k+1]); output at O_k.
 struct MergeJob {
     int kind;
     int K;
-    int64_t N, L;
+    Inst in;
+    int64_t n_B;
+    int64_t N;                       // extent of the key arrays
     int64_t W, gpb;                  // kind 0
-    const int64_t* splits;           // kind 1
-    const int64_t* offsets;          // kind 1
+    const int64_t* splits;           // kind 1: rows (inst*n_B + b), n_P+1 columns
+    const int64_t* offsets;          // kind 1: rows inst, n_P+1 absolute offsets
     int64_t n_P;                     // kind 1
     __device__ __forceinline__ void run(int64_t g, int r, int64_t& lo, int64_t& hi) const
     {
         if (kind == 0) {
-            int64_t b = g / gpb, gi = g - b * gpb;
-            int64_t bs = b * L < N ? b * L : N;
-            int64_t be = bs + L < N ? bs + L : N;
-            int64_t s = bs + (gi * K + r) * W;
-            lo = s < be ? s : be;
-            hi = s + W < be ? s + W : be;
+            const int64_t gpi = n_B * gpb, inst = g / gpi, lg = g - inst * gpi;
+            const int64_t b = lg / gpb, gi = lg - b * gpb;
+            int64_t bs, be;
+            block_bounds(in.len(inst), n_B, b, bs, be);
+            const int64_t o = in.off(inst), s = bs + (gi * K + r) * W;
+            lo = o + (s < be ? s : be);
+            hi = o + (s + W < be ? s + W : be);
         } else {
-            int64_t bs = (int64_t)r * L < N ? (int64_t)r * L : N;
-            lo = bs + splits[(int64_t)r * (n_P + 1) + g];
-            hi = bs + splits[(int64_t)r * (n_P + 1) + g + 1];
+            const int64_t inst = g / n_P, k = g - inst * n_P;
+            int64_t bs, be;
+            block_bounds(in.len(inst), n_B, r, bs, be);
+            const int64_t* row = splits + (inst * n_B + r) * (n_P + 1);
+            lo = in.off(inst) + bs + row[k];
+            hi = in.off(inst) + bs + row[k + 1];
         }
     }
     __device__ __forceinline__ int64_t out_base(int64_t g) const
     {
         if (kind == 0) {
-            int64_t b = g / gpb, gi = g - b * gpb;
-            int64_t bs = b * L < N ? b * L : N;
-            int64_t be = bs + L < N ? bs + L : N;
-            int64_t s = bs + gi * K * W;
-            return s < be ? s : be;
+            const int64_t gpi = n_B * gpb, inst = g / gpi, lg = g - inst * gpi;
+            const int64_t b = lg / gpb, gi = lg - b * gpb;
+            int64_t bs, be;
+            block_bounds(in.len(inst), n_B, b, bs, be);
+            const int64_t s = bs + gi * K * W;
+            return in.off(inst) + (s < be ? s : be);
         }
-        return offsets[g];
+        const int64_t inst = g / n_P, k = g - inst * n_P;
+        return offsets[inst * (n_P + 1) + k];
     }
     // number of elements of group g
     __device__ __forceinline__ int64_t size(int64_t g) const
     {
         if (kind == 0) {
-            int64_t b = g / gpb;
-            int64_t bs = b * L < N ? b * L : N;
-            int64_t be = bs + L < N ? bs + L : N;
-            int64_t s = out_base(g), e = s + (int64_t)K * W;
-            return (e < be ? e : be) - s;
+            const int64_t gpi = n_B * gpb, inst = g / gpi, lg = g - inst * gpi;
+            const int64_t b = lg / gpb;
+            int64_t bs, be;
+            block_bounds(in.len(inst), n_B, b, bs, be);
+            const int64_t s = out_base(g), e = s + (int64_t)K * W, end = in.off(inst) + be;
+            return (e < end ? e : end) - s;
         }
-        return offsets[g + 1] - offsets[g];
+        const int64_t inst = g / n_P, k = g - inst * n_P;
+        return offsets[inst * (n_P + 1) + k + 1] - offsets[inst * (n_P + 1) + k];
     }
 };
 
@@ -1026,73 +1069,96 @@ __global__ void __launch_bounds__(NT) k_merge(Level C, GBuf<K> src, GBuf<K> dst,
 // ------------------------------------------------------------ step 2 and 3
 // Regular sampling (Sec. 2.3): sample j (1..n_P-1) of non-empty sorted block
 // b of length m is block[floor(j*m/n_P)].  Trailing blocks are the only
-// empty ones, so the non-empty blocks are b < nb1.
+// empty ones, so the non-empty blocks of an instance are b < ceil(N/L).
+// Samples of (instance, block) occupy row inst*n_B + b of n_P-1 slots.
 template <typename K>
-__global__ void k_psrs_samples(GBuf<K> blk, GBuf<K> samples, int64_t N, int64_t L, int64_t nb1, int64_t n_P)
+__global__ void k_psrs_samples(GBuf<K> blk, GBuf<K> samples, Inst in, int64_t n_B, int64_t n_P)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per = n_P - 1;
-    if (idx >= nb1 * per) return;
-    const int64_t b = idx / per, j = idx - b * per + 1;
-    const int64_t bs = b * L, be = bs + L < N ? bs + L : N;
+    if (idx >= in.count * n_B * per) return;
+    const int64_t row = idx / per, j = idx - row * per + 1;
+    const int64_t inst = row / n_B, b = row - inst * n_B;
+    int64_t bs, be;
+    block_bounds(in.len(inst), n_B, b, bs, be);
     const int64_t m = be - bs;
+    if (m <= 0) return;
     const int64_t pos = (int64_t)(((unsigned __int128)j * (uint64_t)m) / (uint64_t)n_P);
     if (!PS_IN(pos, m, 33)) return;
-    samples.st(idx, blk.ld(bs + pos));
+    samples.st(idx, blk.ld(in.off(inst) + bs + pos));
 }
 
-// PSRS pivot k = element of rank (k-1)*nb1 + floor((nb1-1)/2) of the sorted
-// pool of samples; the pool is nb1 sorted lists, so the rank is found by the
-// same value bisection as exact splitting, without sorting the pool.
+// PSRS pivot k of an instance = element of rank (k-1)*nb1 + floor((nb1-1)/2)
+// of its sorted pool of samples; the pool is nb1 sorted lists, so the rank is
+// found by the same value bisection as exact splitting, without sorting the
+// pool.  One CTA per (instance, pivot).
 template <int NT, typename K>
-__global__ void __launch_bounds__(NT) k_psrs_select(GBuf<K> samples, int64_t nb1, int64_t n_P, K* piv)
+__global__ void __launch_bounds__(NT) k_psrs_select(GBuf<K> samples, Inst in, int64_t n_B, int64_t n_P, K* piv)
 {
     extern __shared__ __align__(16) char smem[];
     int64_t* a = (int64_t*)smem;
-    int64_t* b = a + nb1;
-    const int64_t k = blockIdx.x + 1;
+    int64_t* b = a + n_B;
+    const int64_t inst = blockIdx.x / (n_P - 1), k = blockIdx.x - inst * (n_P - 1) + 1;
+    const int64_t N = in.len(inst);
+    if (N <= 0) {
+        if (threadIdx.x == 0) piv[blockIdx.x] = KT<K>::from_u(0);
+        return;
+    }
+    const int64_t L = (N + n_B - 1) / n_B;
+    const int64_t nb1 = (N + L - 1) / L;
     const int64_t per = n_P - 1;
     for (int64_t r = threadIdx.x; r < nb1; r += NT) {
-        a[r] = r * per;
-        b[r] = (r + 1) * per;
+        a[r] = (inst * n_B + r) * per;
+        b[r] = a[r] + per;
     }
     __syncthreads();
     const int64_t q = (k - 1) * nb1 + (nb1 - 1) / 2;
-    K v = select_value<NT, K>(samples, a, b, (int)nb1, q + 1);
-    if (threadIdx.x == 0) piv[k - 1] = v;
+    const K v = select_value<NT, K>(samples, a, b, (int)nb1, q + 1);
+    if (threadIdx.x == 0) piv[blockIdx.x] = v;
 }
 
 // PSRS splits: s[b][k] = number of elements <= P_k in sorted block b.
 template <typename K>
-__global__ void k_psrs_splits(GBuf<K> blk, const K* piv, int64_t N, int64_t L, int64_t n_B, int64_t n_P,
-                              int64_t* splits)
+__global__ void k_psrs_splits(GBuf<K> blk, const K* piv, Inst in, int64_t n_B, int64_t n_P, int64_t* splits)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_B * (n_P - 1)) return;
-    const int64_t b = idx / (n_P - 1), k = idx - b * (n_P - 1) + 1;
-    const int64_t bs = b * L < N ? b * L : N;
-    const int64_t be = bs + L < N ? bs + L : N;
-    splits[b * (n_P + 1) + k] = bound<false>(blk, bs, be, piv[k - 1]);
+    if (idx >= in.count * n_B * (n_P - 1)) return;
+    const int64_t row = idx / (n_P - 1), k = idx - row * (n_P - 1) + 1;
+    const int64_t inst = row / n_B, b = row - inst * n_B;
+    int64_t bs, be;
+    block_bounds(in.len(inst), n_B, b, bs, be);
+    const int64_t o = in.off(inst);
+    splits[row * (n_P + 1) + k] = bound<false>(blk, o + bs, o + be, piv[inst * (n_P - 1) + k - 1]);
 }
 
 // PSES (Sec. 2.3): r_k = floor(k*N/n_P); P_k = smallest v with #{x <= v} >=
 // max(r_k, 1) (Eq. 1); c_k = r_k - #{x < P_k} (Eq. 2); split of block b =
 // #{x < P_k in b} plus the copies of P_k it contributes, taken greedily in
-// block order until c_k copies are placed.  One CTA per pivot.
+// block order until c_k copies are placed.  One CTA per (instance, pivot).
 template <int NT, typename K>
-__global__ void __launch_bounds__(NT) k_pses(GBuf<K> blk, int64_t N, int64_t L, int64_t n_B, int64_t n_P, K* piv,
+__global__ void __launch_bounds__(NT) k_pses(GBuf<K> blk, Inst in, int64_t n_B, int64_t n_P, K* piv,
                                              int64_t* cvec, int64_t* splits)
 {
     extern __shared__ __align__(16) char smem[];
     int64_t* a = (int64_t*)smem;
     int64_t* b = a + n_B;
-    const int64_t k = blockIdx.x + 1;
+    const int64_t inst = blockIdx.x / (n_P - 1), k = blockIdx.x - inst * (n_P - 1) + 1;
+    const int64_t N = in.len(inst), o = in.off(inst);
     for (int64_t r = threadIdx.x; r < n_B; r += NT) {
-        int64_t bs = r * L < N ? r * L : N;
-        a[r] = bs;
-        b[r] = bs + L < N ? bs + L : N;
+        int64_t bs, be;
+        block_bounds(N, n_B, r, bs, be);
+        a[r] = o + bs;
+        b[r] = o + be;
     }
     __syncthreads();
+    if (N <= 0) {
+        for (int64_t r = threadIdx.x; r < n_B; r += NT) splits[(inst * n_B + r) * (n_P + 1) + k] = 0;
+        if (threadIdx.x == 0) {
+            piv[blockIdx.x] = KT<K>::from_u(0);
+            cvec[blockIdx.x] = 0;
+        }
+        return;
+    }
     const int64_t rk = (int64_t)(((unsigned __int128)k * (uint64_t)N) / (uint64_t)n_P);
     const K v = select_value<NT, K>(blk, a, b, (int)n_B, rk > 0 ? rk : 1);
     const int per = (int)((n_B + NT - 1) / NT);
@@ -1114,36 +1180,39 @@ __global__ void __launch_bounds__(NT) k_pses(GBuf<K> blk, int64_t N, int64_t L, 
         if (rem < 0) rem = 0;
         int64_t take = eq < rem ? eq : rem;
         pre += eq;
-        splits[(int64_t)r * (n_P + 1) + k] = lb + take;
+        splits[(inst * n_B + r) * (n_P + 1) + k] = lb + take;
     }
     if (threadIdx.x == 0) {
-        piv[k - 1] = v;
-        cvec[k - 1] = ck;
+        piv[blockIdx.x] = v;
+        cvec[blockIdx.x] = ck;
     }
 }
 
 // Split-table borders: s[b][0] = 0 and s[b][n_P] = block length.
 template <int DUMMY = 0>
-__global__ void k_split_borders(int64_t N, int64_t L, int64_t n_B, int64_t n_P, int64_t* splits)
+__global__ void k_split_borders(Inst in, int64_t n_B, int64_t n_P, int64_t* splits)
 {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_B) return;
-    const int64_t bs = b * L < N ? b * L : N;
-    const int64_t be = bs + L < N ? bs + L : N;
-    splits[b * (n_P + 1)] = 0;
-    splits[b * (n_P + 1) + n_P] = be - bs;
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= in.count * n_B) return;
+    const int64_t inst = row / n_B, b = row - inst * n_B;
+    int64_t bs, be;
+    block_bounds(in.len(inst), n_B, b, bs, be);
+    splits[row * (n_P + 1)] = 0;
+    splits[row * (n_P + 1) + n_P] = be - bs;
 }
 
-// O_k = sum over blocks of s[b][k]: the elements of partitions 0..k-1, i.e.
-// the exclusive scan of the partition totals (Sec. 2), for k = 0..n_P.
+// O_k = off(instance) + sum over its blocks of s[b][k]: the elements of
+// partitions 0..k-1, i.e. the exclusive scan of the partition totals (Sec. 2),
+// for k = 0..n_P, as absolute positions.
 template <int DUMMY = 0>
-__global__ void k_offsets(const int64_t* splits, int64_t n_B, int64_t n_P, int64_t* offsets)
+__global__ void k_offsets(const int64_t* splits, Inst in, int64_t n_B, int64_t n_P, int64_t* offsets)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > n_P) return;
-    int64_t s = 0;
-    for (int64_t b = 0; b < n_B; b++) s += splits[b * (n_P + 1) + k];
-    offsets[k] = s;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= in.count * (n_P + 1)) return;
+    const int64_t inst = idx / (n_P + 1), k = idx - inst * (n_P + 1);
+    int64_t s = in.off(inst);
+    for (int64_t b = 0; b < n_B; b++) s += splits[(inst * n_B + b) * (n_P + 1) + k];
+    offsets[idx] = s;
 }
 
 // Trace output: pivots back in the caller's representation.

@@ -54,8 +54,13 @@ template <typename K> struct Plan {
     static constexpr int T = Cfg<K>::TNT * Cfg<K>::TE;    // tile
     static constexpr int CAP = Cfg<K>::MNT * Cfg<K>::ME;  // merge chunk capacity
     static constexpr int POOL = Cfg<K>::PNT * Cfg<K>::PE;
-    int64_t N, n_B, n_P, L, R0;
+    int64_t N;      // extent of the key arrays
+    int64_t n_inst; // instances (1 for a single sort)
+    int64_t Nmax;   // longest instance
+    int64_t Nsum;   // keys over all instances
+    int64_t n_B, n_P, L, R0;
     int mode;
+    bool direct;    // n_B = n_P = 1: the block sort is the whole sort
     int npass;
     int64_t F[16];
     MergeShape inblock[16], fin;
@@ -90,7 +95,7 @@ template <typename K> struct Plan {
             int64_t c = cnom();
             for (int q = 0; q < m.nlev - 1 - l; q++) c *= jl;
             m.cnom[l] = c;
-            m.G[l + 1] = N / c + m.G[l] + 1;
+            m.G[l + 1] = Nsum / c + m.G[l] + 1;
         }
         size_t o = 0;
         for (int l = 0; l <= m.nlev; l++) {
@@ -119,14 +124,18 @@ template <typename K> struct Plan {
         return m;
     }
 
-    void make(int64_t n, int64_t nb, int64_t np, int md)
+    void make(int64_t extent, int64_t ninst, int64_t nmax, int64_t nsum, int64_t nb, int64_t np, int md)
     {
-        N = n;
+        N = extent;
+        n_inst = ninst;
+        Nmax = nmax;
+        Nsum = nsum;
         n_B = nb;
         n_P = np;
         mode = md;
-        L = (N + n_B - 1) / n_B;
-        R0 = (L + T - 1) / T;
+        direct = n_B == 1 && n_P == 1;
+        L = (Nmax + n_B - 1) / n_B;
+        R0 = std::max<int64_t>(1, (L + T - 1) / T);
         npass = 0;
         for (int64_t x = R0; x > 1; x = (x + FMAX - 1) / FMAX) npass++;
         size_t mbytes = 0;
@@ -143,27 +152,29 @@ template <typename K> struct Plan {
             F[p] = std::min<int64_t>(f, R);
             const int64_t Rp = (L + W - 1) / W;
             const int64_t gpb = (Rp + F[p] - 1) / F[p];
-            inblock[p] = shape((int)F[p], n_B * gpb, std::min<int64_t>(F[p] * W, L));
+            inblock[p] = shape((int)F[p], n_inst * n_B * gpb, std::min<int64_t>(F[p] * W, L));
             mbytes = std::max(mbytes, inblock[p].bytes);
             R = (R + F[p] - 1) / F[p];
             W *= F[p];
         }
-        const int64_t mmax = mode == PS_PIVOT_EXACT ? (N + n_P - 1) / n_P + 1 : N;
-        fin = shape((int)n_B, n_P, mmax);
-        mbytes = std::max(mbytes, fin.bytes);
+        const int64_t mmax = mode == PS_PIVOT_EXACT ? (Nmax + n_P - 1) / n_P + 1 : Nmax;
+        if (!direct) {
+            fin = shape((int)n_B, n_inst * n_P, mmax);
+            mbytes = std::max(mbytes, fin.bytes);
+        }
         size_t o = 0;
         o_data = o;
         o += align256((size_t)N * GStore<K>::bytes + 256);
         o_split = o;
-        o += align256((size_t)n_B * (n_P + 1) * 8);
+        o += align256((size_t)n_inst * n_B * (n_P + 1) * 8);
         o_off = o;
-        o += align256((size_t)(n_P + 1) * 8);
+        o += align256((size_t)n_inst * (n_P + 1) * 8);
         o_piv = o;
-        o += align256((size_t)n_P * sizeof(K));
+        o += align256((size_t)n_inst * n_P * sizeof(K));
         o_c = o;
-        o += align256((size_t)n_P * 8);
+        o += align256((size_t)n_inst * n_P * 8);
         o_samp = o;
-        o += align256((size_t)n_B * std::max<int64_t>(n_P - 1, 1) * GStore<K>::bytes + 256);
+        o += align256((size_t)n_inst * n_B * std::max<int64_t>(n_P - 1, 1) * GStore<K>::bytes + 256);
         o_merge = o;
         o += mbytes;
         total = o;
@@ -179,9 +190,11 @@ template <> inline GBuf<Rec> gbuf_at<Rec>(char* base, int64_t n)
 }
 
 template <typename K> static GBuf<K> gbuf_user(const SortArgs& a);
-template <> inline GBuf<uint32_t> gbuf_user<uint32_t>(const SortArgs& a) { return GBuf<uint32_t>{(uint32_t*)a.keys, a.n}; }
-template <> inline GBuf<uint64_t> gbuf_user<uint64_t>(const SortArgs& a) { return GBuf<uint64_t>{(uint64_t*)a.keys, a.n}; }
-template <> inline GBuf<Rec> gbuf_user<Rec>(const SortArgs& a) { return GBuf<Rec>{(uint64_t*)a.keys, a.payload, a.n}; }
+// the caller's arrays span the single sort, or every segment of a batch
+static inline int64_t user_extent(const SortArgs& a) { return a.inst_base ? a.extent : a.n; }
+template <> inline GBuf<uint32_t> gbuf_user<uint32_t>(const SortArgs& a) { return GBuf<uint32_t>{(uint32_t*)a.keys, user_extent(a)}; }
+template <> inline GBuf<uint64_t> gbuf_user<uint64_t>(const SortArgs& a) { return GBuf<uint64_t>{(uint64_t*)a.keys, user_extent(a)}; }
+template <> inline GBuf<Rec> gbuf_user<Rec>(const SortArgs& a) { return GBuf<Rec>{(uint64_t*)a.keys, a.payload, user_extent(a)}; }
 
 template <typename K> static bool same_buf(const GBuf<K>& x, const GBuf<K>& y);
 template <> inline bool same_buf<uint32_t>(const GBuf<uint32_t>& x, const GBuf<uint32_t>& y) { return x.p == y.p; }
@@ -213,15 +226,27 @@ template <typename K> struct Pipeline {
     static size_t big_smem(int Kr) { return SBuf<K>::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
     static size_t tile_smem() { return SBuf<K>::bytes(T) + 64; }
 
-    template <int XF>
-    static cudaError_t tile_sort(GBuf<K> src, GBuf<K> dst, const Plan<K>& pl, cudaStream_t s)
+    static Inst inst_of(const Plan<K>& pl, const SortArgs& a)
     {
-        auto f = k_tile_sort<TNT, TE, K, XF>;
+        Inst in;
+        in.base = a.inst_base;
+        in.n = a.inst_n;
+        in.count = pl.n_inst;
+        in.n0 = pl.Nmax;
+        return in;
+    }
+
+    template <int XF>
+    static cudaError_t tile_sort(GBuf<K> src, GBuf<K> dst, const Plan<K>& pl, const SortArgs& a_, cudaStream_t s)
+    {
+        // the tile sort is the whole sort when there is one block, one
+        // partition and no in-block pass
+        auto f = (pl.direct && pl.npass == 0) ? k_tile_sort<TNT, TE, K, XF, true> : k_tile_sort<TNT, TE, K, XF, false>;
         cudaError_t e = smem_attr(f, tile_smem());
         if (e != cudaSuccess) return e;
-        const int64_t grid = pl.n_B * pl.R0;
+        const int64_t grid = pl.n_inst * pl.n_B * pl.R0;
         ProfScope ps_("tile_sort", s);
-        f<<<(unsigned)grid, TNT, tile_smem(), s>>>(src, dst, pl.N, pl.L, pl.R0);
+        f<<<(unsigned)grid, TNT, tile_smem(), s>>>(src, dst, inst_of(pl, a_), pl.n_B, pl.R0);
         return cudaGetLastError();
     }
 
@@ -301,78 +326,91 @@ template <typename K> struct Pipeline {
         cudaStream_t s = a.stream;
         GBuf<K> user = gbuf_user<K>(a);
         GBuf<K> wsb = gbuf_at<K>(ws + pl.o_data, pl.N);
+        const Inst in = inst_of(pl, a);
         cudaError_t e;
-        // Step 1: sort each block (tiles, then in-block merge passes).
-        GBuf<K> cur = (pl.npass % 2 == 0) ? wsb : user;
-        if ((e = tile_sort<XF>(user, cur, pl, s)) != cudaSuccess) return e;
+        // Step 1: sort each block (tiles, then in-block merge passes).  The
+        // passes alternate between the caller's buffer and the workspace copy;
+        // the block sort ends in the workspace, or in the caller's buffer when
+        // it is the whole sort (one block, one partition).
+        const bool end_in_user = pl.direct;
+        GBuf<K> cur = ((pl.npass % 2 == 0) != end_in_user) ? wsb : user;
+        if ((e = tile_sort<XF>(user, cur, pl, a, s)) != cudaSuccess) return e;
         int64_t W = T;
         for (int p = 0; p < pl.npass; p++) {
             MergeJob job{};  // in-block pass p
             job.kind = 0;
             job.K = (int)pl.F[p];
+            job.in = in;
+            job.n_B = pl.n_B;
             job.N = pl.N;
-            job.L = pl.L;
             job.W = W;
-            int64_t Rp = (pl.L + W - 1) / W;
+            const int64_t Rp = (pl.L + W - 1) / W;
             job.gpb = (Rp + pl.F[p] - 1) / pl.F[p];
             GBuf<K> nxt = same_buf(cur, wsb) ? user : wsb;
-            if ((e = merge<0>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) return e;
+            if (p + 1 == pl.npass && end_in_user) {
+                if ((e = merge<XF>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) return e;
+            } else if ((e = merge<0>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) {
+                return e;
+            }
             cur = nxt;
             W *= pl.F[p];
         }
+        if (pl.direct && !(a.trace && pl.n_inst == 1)) return cudaGetLastError();
         // Steps 2 and 3: pivots, split table, offsets.
         int64_t* splits = (int64_t*)(ws + pl.o_split);
         int64_t* offs = (int64_t*)(ws + pl.o_off);
         K* piv = (K*)(ws + pl.o_piv);
         int64_t* cvec = (int64_t*)(ws + pl.o_c);
+        const int64_t nrows = pl.n_inst * pl.n_B;
         {
             ProfScope ps_("split_borders", s);
-            k_split_borders<<<(unsigned)((pl.n_B + 255) / 256), 256, 0, s>>>(pl.N, pl.L, pl.n_B, pl.n_P, splits);
+            k_split_borders<<<(unsigned)((nrows + 255) / 256), 256, 0, s>>>(in, pl.n_B, pl.n_P, splits);
         }
         if (pl.n_P > 1) {
+            const int64_t npiv = pl.n_inst * (pl.n_P - 1);
             if (a.mode == PS_PIVOT_EXACT) {
                 auto f = k_pses<512, K>;
                 size_t sm = 16 * (size_t)pl.n_B + 64;
                 if ((e = smem_attr(f, sm)) != cudaSuccess) return e;
                 ProfScope ps_("pses", s);
-                f<<<(unsigned)(pl.n_P - 1), 512, sm, s>>>(cur, pl.N, pl.L, pl.n_B, pl.n_P, piv, cvec, splits);
+                f<<<(unsigned)npiv, 512, sm, s>>>(cur, in, pl.n_B, pl.n_P, piv, cvec, splits);
             } else {
-                const int64_t nb1 = (pl.N + pl.L - 1) / pl.L;
-                GBuf<K> samp = gbuf_at<K>(ws + pl.o_samp, pl.n_B * (pl.n_P - 1));
-                const int64_t ns = nb1 * (pl.n_P - 1);
+                GBuf<K> samp = gbuf_at<K>(ws + pl.o_samp, nrows * (pl.n_P - 1));
+                const int64_t ns = nrows * (pl.n_P - 1);
                 {
                     ProfScope ps_("psrs_samples", s);
-                    k_psrs_samples<K><<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(cur, samp, pl.N, pl.L, nb1, pl.n_P);
+                    k_psrs_samples<K><<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(cur, samp, in, pl.n_B, pl.n_P);
                 }
                 auto f = k_psrs_select<512, K>;
-                size_t sm = 16 * (size_t)nb1 + 64;
+                size_t sm = 16 * (size_t)pl.n_B + 64;
                 if ((e = smem_attr(f, sm)) != cudaSuccess) return e;
                 {
                     ProfScope ps_("psrs_select", s);
-                    f<<<(unsigned)(pl.n_P - 1), 512, sm, s>>>(samp, nb1, pl.n_P, piv);
+                    f<<<(unsigned)npiv, 512, sm, s>>>(samp, in, pl.n_B, pl.n_P, piv);
                 }
-                const int64_t nt = pl.n_B * (pl.n_P - 1);
                 ProfScope ps_("psrs_splits", s);
-                k_psrs_splits<K><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(cur, piv, pl.N, pl.L, pl.n_B,
-                                                                             pl.n_P, splits);
+                k_psrs_splits<K><<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(cur, piv, in, pl.n_B, pl.n_P, splits);
             }
         }
         {
             ProfScope ps_("offsets", s);
-            k_offsets<<<(unsigned)((pl.n_P + 1 + 255) / 256), 256, 0, s>>>(splits, pl.n_B, pl.n_P, offs);
+            const int64_t no = pl.n_inst * (pl.n_P + 1);
+            k_offsets<<<(unsigned)((no + 255) / 256), 256, 0, s>>>(splits, in, pl.n_B, pl.n_P, offs);
         }
-        // Step 4: merge the k-th partitions of all blocks into the caller's buffer.
+        // Step 4: merge the k-th partitions of all blocks into the caller's
+        // buffer (nothing to merge when the block sort was the whole sort).
         MergeJob job{};
         job.kind = 1;
         job.K = (int)pl.n_B;
+        job.in = in;
+        job.n_B = pl.n_B;
         job.N = pl.N;
-        job.L = pl.L;
         job.splits = splits;
         job.offsets = offs;
         job.n_P = pl.n_P;
-        if ((e = merge<XF>(job, pl.fin, cur, user, pl, ws, s)) != cudaSuccess) return e;
-        // Trace.
-        if (a.trace) {
+        if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, user, pl, ws, s)) != cudaSuccess) return e;
+        // Trace (single sorts only).
+        if (a.trace && pl.n_inst == 1) {
             const ps_trace* t = a.trace;
             if (t->pivots && pl.n_P > 1) {
                 GBuf<K> tp = trace_buf(t);
@@ -400,10 +438,18 @@ template <typename K> struct Pipeline {
 
     static GBuf<K> trace_buf(const ps_trace* t);
 
+    static void make_plan(Plan<K>& pl, const SortArgs& a)
+    {
+        if (a.inst_base)
+            pl.make(a.extent, a.n_inst, a.n_max, a.n_sum, a.n_B, a.n_P, a.mode);
+        else
+            pl.make(a.n, 1, a.n, a.n, a.n_B, a.n_P, a.mode);
+    }
+
     static int run(const SortArgs& a)
     {
         Plan<K> pl;
-        pl.make(a.n, a.n_B, a.n_P, a.mode);
+        make_plan(pl, a);
         char* ws = nullptr;
         int rc = ws_alloc((void**)&ws, pl.total, a.stream);
         if (rc != PS_OK) return rc;
@@ -423,7 +469,7 @@ template <typename K> struct Pipeline {
     static int run_on(const SortArgs& a, char* ws, size_t cap)
     {
         Plan<K> pl;
-        pl.make(a.n, a.n_B, a.n_P, a.mode);
+        make_plan(pl, a);
         if (pl.total > cap) return PS_ERR_INVALID_ARG;
         cudaError_t e;
         switch (xf_of(a.dtype)) {
@@ -438,7 +484,7 @@ template <typename K> struct Pipeline {
     static size_t ws_bytes(int64_t n, int64_t nb, int64_t np)
     {
         Plan<K> pl;
-        pl.make(n, nb, np, PS_PIVOT_REGULAR);
+        pl.make(n, 1, n, n, nb, np, PS_PIVOT_REGULAR);
         return pl.total;
     }
 };

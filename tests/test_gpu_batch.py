@@ -1,0 +1,117 @@
+"""ps_sort_batch: every segment of a batch must come out exactly as the
+method sorts it alone (the unique sorted permutation), whatever the mix of
+segment lengths -- empty, one key, one tile, several tiles, several blocks."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2305_05245_gb300 as ps
+    assert torch.cuda.is_available()
+    return ps
+
+
+def make_batch(n_segs, max_log, dtype, dist, seed, special=()):
+    z = synth.splitmix64(seed, n_segs)
+    u = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    lens = np.floor(2.0 ** (u * max_log)).astype(np.int64) - 1
+    lens[: len(special)] = special
+    offs = np.zeros(n_segs + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    keys = synth.keys(int(offs[-1]), dtype, dist, seed=seed + 1)
+    return keys, offs
+
+
+def reference(ora, keys, offs):
+    """Each segment sorted alone (plain definition: stable argsort on the order
+    key within each segment)."""
+    seg = np.repeat(np.arange(len(offs) - 1), np.diff(offs))
+    idx = np.lexsort((ora.order_key(keys), seg))
+    return keys[idx]
+
+
+def to_dev(a):
+    import torch
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32).copy()).cuda()
+    return torch.from_numpy(a.copy()).cuda()
+
+
+SPECIAL = [0, 1, 2, 8191, 8192, 8193, 16385, 70_000, 300_001, 1 << 20]
+
+
+@pytest.mark.parametrize("dtype,dist", [("int32", "uniform"), ("int64", "few_unique"),
+                                        ("float32", "gaussian"), ("float64", "uniform"),
+                                        ("uint32", "three_valued"), ("int64", "sorted")])
+@pytest.mark.parametrize("mode", ["regular", "exact"])
+def test_batch_matches_reference(ps, ora, dtype, dist, mode):
+    import torch
+    keys, offs = make_batch(600, 17, dtype, dist, seed=synth.seed_for("batch", dtype, dist) % 100000,
+                            special=SPECIAL)
+    x = to_dev(keys)
+    if dtype == "uint32":
+        from paper_2305_05245_gb300 import _lib
+        import ctypes
+        o = torch.from_numpy(offs).cuda()
+        rc = _lib.load().ps_sort_batch(ctypes.c_void_p(o.data_ptr()), len(offs) - 1,
+                                       ctypes.c_void_p(x.data_ptr()), 4, 1 if mode == "exact" else 0, None)
+        assert rc == 0
+    else:
+        ps.sort_batch(x, torch.from_numpy(offs).cuda(), mode)
+    torch.cuda.synchronize()
+    got = x.cpu().numpy().view(keys.dtype)
+    want = reference(ora, keys, offs)
+    assert got.tobytes() == want.tobytes()
+
+
+def test_batch_equals_per_segment_sort(ps):
+    import torch
+    keys, offs = make_batch(60, 19, "int64", "uniform", seed=7, special=[8193, 1 << 18, 3])
+    x = to_dev(keys)
+    ps.sort_batch(x, torch.from_numpy(offs).cuda(), "exact")
+    y = to_dev(keys)
+    for i in range(len(offs) - 1):
+        seg = y[offs[i]:offs[i + 1]]
+        if seg.numel() > 1:
+            ps.sort(seg, "exact")
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
+def test_batch_config4_shape(ps, ora):
+    """Lengths log-uniform in [2^6, 2^22] (the batched benchmark's shape), 64
+    segments, int32 and float32, uniform and few-unique keys."""
+    import torch
+    for dtype, dist in (("int32", "uniform"), ("float32", "few_unique")):
+        z = synth.splitmix64(11, 64)
+        u = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        lens = np.floor(2.0 ** (6 + 16 * u)).astype(np.int64)
+        offs = np.zeros(65, dtype=np.int64)
+        offs[1:] = np.cumsum(lens)
+        keys = synth.keys(int(offs[-1]), dtype, dist, seed=12)
+        x = to_dev(keys)
+        ps.sort_batch(x, torch.from_numpy(offs).cuda(), "exact")
+        torch.cuda.synchronize()
+        assert x.cpu().numpy().tobytes() == reference(ora, keys, offs).tobytes()
+
+
+def test_batch_argument_errors(ps):
+    import ctypes
+    import torch
+    from paper_2305_05245_gb300 import _lib
+    lib = _lib.load()
+    x = torch.zeros(10, dtype=torch.int32, device="cuda")
+    bad = torch.tensor([0, 5, 3, 10], dtype=torch.int64, device="cuda")  # decreasing
+    assert lib.ps_sort_batch(ctypes.c_void_p(bad.data_ptr()), 3, ctypes.c_void_p(x.data_ptr()), 0, 1, None) == -1
+    assert lib.ps_sort_batch(None, 0, None, 0, 1, None) == 0
+    assert lib.ps_sort_batch(ctypes.c_void_p(bad.data_ptr()), 3, ctypes.c_void_p(x.data_ptr()), 9, 1, None) == -2
