@@ -148,6 +148,32 @@ const char* ps_status_string(int status);
  * none). */
 int ps_last_cuda_error(void);
 
+/* ---- sort server (continuous batching) ------------------------------------
+ * A server sorts device buffers submitted from any host thread.  Requests
+ * queue in arrival order; a worker thread admits the queue's head whenever a
+ * stream slot is free, fewer than max_inflight requests are on the GPU and the
+ * memory budget holds the request's cost (a staging copy of its keys plus the
+ * sort's workspace).  Each admission round is gathered into one batched sort
+ * per (dtype, pivot mode), run on one of several server streams, so rounds
+ * admitted while others run overlap on the GPU.  Results are bit-identical to
+ * ps_sort on each buffer alone.
+ *   ps_server_open    budget in bytes (> 0), max_inflight >= 1; the server
+ *                     uses the device current at open.
+ *   ps_server_submit  dev_keys must hold the n keys when submitted (ordered
+ *                     before the call on the caller's side) and stay untouched
+ *                     until the request completes; writes a request id.
+ *                     PS_ERR_BUSY if the request alone exceeds the budget;
+ *                     PS_ERR_INVALID_ARG after ps_server_close started.
+ *   ps_server_poll    non-blocking: moves up to cap completed (id, status)
+ *                     pairs out, in completion order, and sets *n_done.
+ *   ps_server_close   stops accepting, waits for every admitted and queued
+ *                     request to finish, frees the server. */
+typedef struct ps_server ps_server;
+int ps_server_open(size_t mem_budget_bytes, int max_inflight, ps_server** out);
+int ps_server_submit(ps_server* server, void* dev_keys, int64_t n, int dtype, int pivot_mode, uint64_t* req_id);
+int ps_server_poll(ps_server* server, uint64_t* done_ids, int* statuses, int cap, int* n_done);
+int ps_server_close(ps_server* server);
+
 /* ---- allocation-free variant -------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory: code running while a CUDA graph is

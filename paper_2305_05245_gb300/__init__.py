@@ -18,7 +18,7 @@ from ._lib import PS_PIVOT_EXACT, PS_PIVOT_REGULAR, PsortError  # noqa: F401
 
 __all__ = ["sort", "sort_pairs", "sort_host", "resolve_params", "workspace_bytes", "Trace",
            "PsortError", "PS_PIVOT_EXACT", "PS_PIVOT_REGULAR", "profile_enable", "profile_read",
-           "profile_reset", "sort_noalloc", "sort_batch"]
+           "profile_reset", "sort_noalloc", "sort_batch", "Server"]
 
 _MODES = {"regular": _lib.PS_PIVOT_REGULAR, "psrs": _lib.PS_PIVOT_REGULAR, 0: 0,
           "exact": _lib.PS_PIVOT_EXACT, "pses": _lib.PS_PIVOT_EXACT, 1: 1}
@@ -223,3 +223,57 @@ def sort_batch(keys, seg_offsets, pivot_mode="exact", stream=None) -> None:
     rc = lib.ps_sort_batch(seg_offsets.data_ptr(), n_segs, keys.data_ptr() if keys.numel() else None,
                            _dtype_code(keys.dtype), _mode(pivot_mode), _stream_handle(stream))
     _lib.check(lib, "ps_sort_batch", rc)
+
+
+class Server:
+    """Sort server with continuous batching (ps_server_*).
+
+        srv = Server(budget_bytes=32 << 30, max_inflight=4096)
+        rid = srv.submit(tensor, "exact")   # tensor sorted in place later
+        for rid, status in srv.poll(): ...
+        srv.close()
+
+    The tensor must be ready (synchronise its stream) before submit and must
+    stay alive and untouched until its id comes back from poll()."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 1024):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self._lib, "ps_server_open",
+                   self._lib.ps_server_open(budget_bytes, max_inflight, ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, keys, pivot_mode="exact", code: int | None = None) -> int:
+        if not keys.is_cuda or keys.dim() != 1 or not keys.is_contiguous():
+            raise ValueError("keys must be a contiguous 1-D CUDA tensor")
+        rid = ctypes.c_uint64()
+        n = keys.numel()
+        rc = self._lib.ps_server_submit(self._h, keys.data_ptr() if n else None, n,
+                                        _dtype_code(keys.dtype) if code is None else code,
+                                        _mode(pivot_mode), ctypes.byref(rid))
+        _lib.check(self._lib, "ps_server_submit", rc)
+        self._keep[rid.value] = keys
+        return rid.value
+
+    def poll(self, cap: int = 4096):
+        ids = (ctypes.c_uint64 * cap)()
+        st = (ctypes.c_int * cap)()
+        n = ctypes.c_int()
+        _lib.check(self._lib, "ps_server_poll", self._lib.ps_server_poll(self._h, ids, st, cap, ctypes.byref(n)))
+        out = [(ids[i], st[i]) for i in range(n.value)]
+        for rid, _ in out:
+            self._keep.pop(rid, None)
+        return out
+
+    def close(self) -> None:
+        if self._h:
+            _lib.check(self._lib, "ps_server_close", self._lib.ps_server_close(self._h))
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

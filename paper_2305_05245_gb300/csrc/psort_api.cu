@@ -197,6 +197,111 @@ static size_t dtype_size(int dtype)
     return (dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32) ? 4 : 8;
 }
 
+size_t sort_ws_bytes(int64_t n, int dtype)
+{
+    ps_params r;
+    resolve(n, dtype, nullptr, &r);
+    switch (dtype) {
+    case PS_I32: case PS_F32: case PS_U32: return ws_bytes_u32(n, r.n_blocks, r.n_parts);
+    case -1: return ws_bytes_rec(n, r.n_blocks, r.n_parts);
+    default: return ws_bytes_u64(n, r.n_blocks, r.n_parts);
+    }
+}
+
+// Batched sort of the segments [off[i], off[i+1]) of `keys` (host offsets):
+// bins by length, one multi-instance pipeline per bin, queued on s.
+int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
+               int64_t* pinned, size_t pinned_cap)
+{
+    const int64_t n_segs = (int64_t)off.size() - 1;
+    if (n_segs <= 0) return PS_OK;
+    if (dtype < PS_I32 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
+    if (!keys) return PS_ERR_INVALID_ARG;
+    const bool narrow = dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32;
+    if ((uintptr_t)keys % (narrow ? 4 : 8) != 0) return PS_ERR_INVALID_ARG;
+    if (off[0] < 0) return PS_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n_segs; i++)
+        if (off[i + 1] < off[i]) return PS_ERR_INVALID_ARG;
+    const int64_t extent = off[(size_t)n_segs];
+    // bins: 0 = fits one tile (one CTA each); b >= 1 = lengths in (T*2^(b-1), T*2^b]
+    const int64_t tile = 8192;
+    std::vector<std::vector<int64_t>> bins(48);
+    for (int64_t i = 0; i < n_segs; i++) {
+        const int64_t len = off[i + 1] - off[i];
+        if (len <= 1) continue;
+        int b = 0;
+        while (len > (tile << b)) b++;
+        bins[b].push_back(i);
+    }
+    // one device array holds every bin's (start, length) pairs
+    size_t total = 0;
+    for (auto& v : bins) total += v.size();
+    if (total == 0) return PS_OK;
+    // the instance table is staged in the caller's pinned buffer when it is
+    // large enough (the copy then stays asynchronous; the caller keeps the
+    // buffer untouched until the stream has passed this point), else in a
+    // local array that must outlive the copy, so the call waits for it
+    std::vector<int64_t> local;
+    int64_t* host = nullptr;
+    if (pinned && pinned_cap >= 2 * total) {
+        host = pinned;
+    } else {
+        local.resize(2 * total);
+        host = local.data();
+    }
+    void* dev = nullptr;
+    int rc = ws_alloc(&dev, 2 * total * 8, s);
+    if (rc != PS_OK) return rc;
+    size_t pos = 0;
+    std::vector<size_t> at(bins.size());
+    for (size_t b = 0; b < bins.size(); b++) {
+        at[b] = pos;
+        for (int64_t i : bins[b]) host[pos++] = off[i];
+        for (int64_t i : bins[b]) host[pos++] = off[i + 1] - off[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(dev, host, 2 * total * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && host != pinned) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ws_free(dev, s);
+        return fail_cuda(e);
+    }
+    for (size_t b = 0; b < bins.size() && rc == PS_OK; b++) {
+        const int64_t cnt = (int64_t)bins[b].size();
+        if (cnt == 0) continue;
+        int64_t nmax = 0, nsum = 0;
+        for (int64_t i : bins[b]) {
+            nmax = std::max<int64_t>(nmax, off[i + 1] - off[i]);
+            nsum += off[i + 1] - off[i];
+        }
+        ps_params r;
+        memset(&r, 0, sizeof(r));
+        if (b == 0) {
+            r.n_blocks = r.n_parts = 1;  // one tile: the block sort is the whole sort
+        } else {
+            resolve(nmax, dtype, nullptr, &r);
+        }
+        SortArgs a;
+        a.keys = keys;
+        a.payload = nullptr;
+        a.n = nmax;
+        a.dtype = dtype;
+        a.mode = mode;
+        a.n_B = r.n_blocks;
+        a.n_P = r.n_parts;
+        a.trace = nullptr;
+        a.stream = s;
+        a.inst_base = (const int64_t*)dev + at[b];
+        a.inst_n = (const int64_t*)dev + at[b] + cnt;
+        a.n_inst = cnt;
+        a.n_max = nmax;
+        a.n_sum = nsum;
+        a.extent = extent;
+        rc = dispatch(a);
+    }
+    ws_free(dev, s);
+    return rc;
+}
+
 }  // namespace ps
 
 using namespace ps;
@@ -230,81 +335,12 @@ int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dt
     if (pivot_mode != PS_PIVOT_REGULAR && pivot_mode != PS_PIVOT_EXACT) return PS_ERR_UNSUPPORTED;
     if (n_segs == 0) return PS_OK;
     if (!seg_offsets || !keys) return PS_ERR_INVALID_ARG;
-    const bool narrow = dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32;
-    if ((uintptr_t)keys % (narrow ? 4 : 8) != 0) return PS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<int64_t> off((size_t)n_segs + 1);
     cudaError_t e = cudaMemcpyAsync(off.data(), seg_offsets, off.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e);
-    if (off[0] < 0) return PS_ERR_INVALID_ARG;
-    for (int64_t i = 0; i < n_segs; i++)
-        if (off[i + 1] < off[i]) return PS_ERR_INVALID_ARG;
-    const int64_t extent = off[(size_t)n_segs];
-    // bins: 0 = fits one tile (one CTA each); b >= 1 = lengths in (T*2^(b-1), T*2^b]
-    const int64_t tile = 8192;
-    std::vector<std::vector<int64_t>> bins(48);
-    for (int64_t i = 0; i < n_segs; i++) {
-        const int64_t len = off[i + 1] - off[i];
-        if (len <= 1) continue;
-        int b = 0;
-        while (len > (tile << b)) b++;
-        bins[b].push_back(i);
-    }
-    // one device array holds every bin's (start, length) pairs
-    size_t total = 0;
-    for (auto& v : bins) total += v.size();
-    if (total == 0) return PS_OK;
-    std::vector<int64_t> host(2 * total);
-    void* dev = nullptr;
-    int rc = ws_alloc(&dev, host.size() * 8, s);
-    if (rc != PS_OK) return rc;
-    size_t pos = 0;
-    std::vector<size_t> at(bins.size());
-    for (size_t b = 0; b < bins.size(); b++) {
-        at[b] = pos;
-        for (int64_t i : bins[b]) host[pos++] = off[i];
-        for (int64_t i : bins[b]) host[pos++] = off[i + 1] - off[i];
-    }
-    e = cudaMemcpyAsync(dev, host.data(), host.size() * 8, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) {
-        ws_free(dev, s);
-        return fail_cuda(e);
-    }
-    for (size_t b = 0; b < bins.size() && rc == PS_OK; b++) {
-        const int64_t cnt = (int64_t)bins[b].size();
-        if (cnt == 0) continue;
-        int64_t nmax = 0, nsum = 0;
-        for (int64_t i : bins[b]) {
-            nmax = std::max<int64_t>(nmax, off[i + 1] - off[i]);
-            nsum += off[i + 1] - off[i];
-        }
-        ps_params r;
-        if (b == 0) {
-            r.n_blocks = r.n_parts = 1;  // one tile: the block sort is the whole sort
-        } else {
-            resolve(nmax, dtype, nullptr, &r);
-        }
-        SortArgs a;
-        a.keys = keys;
-        a.payload = nullptr;
-        a.n = nmax;
-        a.dtype = dtype;
-        a.mode = pivot_mode;
-        a.n_B = r.n_blocks;
-        a.n_P = r.n_parts;
-        a.trace = nullptr;
-        a.stream = s;
-        a.inst_base = (const int64_t*)dev + at[b];
-        a.inst_n = (const int64_t*)dev + at[b] + cnt;
-        a.n_inst = cnt;
-        a.n_max = nmax;
-        a.n_sum = nsum;
-        a.extent = extent;
-        rc = dispatch(a);
-    }
-    ws_free(dev, s);
-    return rc;
+    return batch_sort(off, keys, dtype, pivot_mode, s, nullptr, 0);
 }
 
 int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode, const ps_params* params, ps_stream_t stream)

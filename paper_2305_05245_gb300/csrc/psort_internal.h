@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/psort.h"
@@ -62,6 +63,13 @@ size_t ws_bytes_rec(int64_t n, int64_t n_B, int64_t n_P);
 int viol_read_u32(unsigned long long* out);
 int viol_read_u64(unsigned long long* out);
 int viol_read_rec(unsigned long long* out);
+// Batched sort of the segments [off[i], off[i+1]) of keys (host offsets).
+// pinned (optional): page-locked host scratch of pinned_cap int64 for the
+// instance table; when given, the call does not wait for the stream.
+int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
+               int64_t* pinned, size_t pinned_cap);
+// Workspace bytes of a single sort of n keys with automatic parameters.
+size_t sort_ws_bytes(int64_t n, int dtype);
 // The same sorts on a caller-provided workspace (allocation-free entry point).
 int run_sort_u32_on(const SortArgs& a, char* ws, size_t cap);
 int run_sort_u64_on(const SortArgs& a, char* ws, size_t cap);
