@@ -48,7 +48,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
-    ap.add_argument("--workload", default="single", choices=["single", "batch"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
+    ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=32.0, help="serve: admission budget")
     ap.add_argument("--segments", type=int, default=20000)
     ap.add_argument("--baseline-segments", type=int, default=2000,
                     help="segments timed with one ps_sort call each (batch workload)")
@@ -265,6 +268,152 @@ def run_batch(a):
     return 0 if ok else 1
 
 
+# ------------------------------------------------------------ served workload
+SERVE_DTYPES = ["int32", "int64", "float32", "float64"]
+SERVE_DISTS = ["uniform", "sorted", "reverse", "few_unique", "gaussian"]
+
+
+def serve_trace(rate: float, duration: float, seed: int):
+    """Poisson arrivals; per request: length floor(2^U), U ~ U[10, 26], a dtype
+    and a distribution (Gaussian only for floating keys), all seeded."""
+    import numpy as np
+    import synth
+    n_max = int(rate * duration * 3 + 100)
+    z = synth.splitmix64(seed, 5 * n_max)
+    u = lambda k: (z[k::5] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    gaps = -np.log(1.0 - u(0)) / rate
+    t = np.cumsum(gaps)
+    m = int(np.searchsorted(t, duration))
+    lens = np.floor(2.0 ** (10.0 + 16.0 * u(1)[:m])).astype(np.int64)
+    dts = (z[2::5][:m] % np.uint64(4)).astype(np.int64)
+    dists = (z[3::5][:m] % np.uint64(5)).astype(np.int64)
+    offs = (z[4::5][:m] >> np.uint64(8)).astype(np.int64)
+    out = []
+    for i in range(m):
+        dt = SERVE_DTYPES[dts[i]]
+        dist = SERVE_DISTS[dists[i]]
+        if dist == "gaussian" and not dt.startswith("float"):
+            dist = "uniform"
+        out.append((float(t[i]), int(lens[i]), dt, dist, int(offs[i])))
+    return out
+
+
+def serve_pools(dev, pool_n: int):
+    """Device pools the requests copy their keys from (one per dtype and
+    distribution; reverse requests read a sorted pool backwards)."""
+    import torch
+    import synth
+    pools = {}
+    for dt in SERVE_DTYPES:
+        for dist in ("uniform", "few_unique", "gaussian"):
+            if dist == "gaussian" and not dt.startswith("float"):
+                continue
+            pools[(dt, dist)] = synth.keys_torch(pool_n, dt, dist, seed=synth.seed_for("pool", dt, dist), device=dev)
+        pools[(dt, "sorted")] = torch.sort(pools[(dt, "uniform")])[0]
+    torch.cuda.synchronize()
+    return pools
+
+
+def make_request(pools, req, pool_n, stream):
+    import torch
+    _, n, dt, dist, off = req
+    if dist == "reverse":
+        src = pools[(dt, "sorted")]
+    else:
+        src = pools[(dt, dist)]
+    o = off % max(1, pool_n - n)
+    with torch.cuda.stream(stream):
+        x = src[o:o + n].flip(0) if dist == "reverse" else src[o:o + n].clone()
+    stream.synchronize()
+    return x
+
+
+def run_serve(a):
+    """NEXT-2: continuous batching server vs serial plain per-request sorting."""
+    import numpy as np
+    import torch
+
+    import paper_2305_05245_gb300 as ps
+    import synth
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    pool_n = 1 << 27
+    pools = serve_pools(dev, pool_n)
+    trace = serve_trace(a.rate, a.duration, synth.seed_for("serve", a.rate, a.duration))
+    client = torch.cuda.Stream(device=dev)
+
+    def serve_once(tr):
+        srv = ps.Server(budget_bytes=int(a.budget_gb * (1 << 30)), max_inflight=4096)
+        t_sub, t_done, keep = {}, {}, {}
+        stop = threading.Event()
+
+        def poller():
+            while not stop.is_set() or len(t_done) < len(t_sub):
+                for rid, st in srv.poll():
+                    t_done[rid] = (time.perf_counter(), st)
+                    keep.pop(rid, None)
+                time.sleep(0.0002)
+
+        th = threading.Thread(target=poller, daemon=True)
+        t0 = time.perf_counter()
+        th.start()
+        cap = 2 * int(a.budget_gb * (1 << 30))     # client-side back-pressure on held buffers
+        for req in tr:
+            now = time.perf_counter() - t0
+            if req[0] > now:
+                time.sleep(req[0] - now)
+            while sum(v.numel() * v.element_size() for v in list(keep.values())) > cap:
+                time.sleep(0.0005)
+            x = make_request(pools, req, pool_n, client)
+            rid = srv.submit(x, a.pivot)
+            t_sub[rid] = time.perf_counter()
+            keep[rid] = x
+        stop.set()
+        th.join(timeout=600)
+        srv.close()
+        lat = sorted(t_done[r][0] - t_sub[r] for r in t_sub)
+        span = max(v[0] for v in t_done.values()) - min(t_sub.values())
+        bad = sum(1 for v in t_done.values() if v[1] != 0)
+        return lat, span, bad
+
+    warm = trace[: min(len(trace), 50)]
+    serve_once([(0.0,) + r[1:] for r in warm])
+    lat, span, bad = serve_once(trace)
+    keys = sum(r[1] for r in trace)
+    # serial plain path: one ps_sort per request, in arrival order, each waited for
+    nb = min(len(trace), max(50, len(trace) // 4))
+    base_lat = []
+    t0 = time.perf_counter()
+    for req in trace[:nb]:
+        now = time.perf_counter() - t0
+        if req[0] > now:
+            time.sleep(req[0] - now)
+        x = make_request(pools, req, pool_n, client)
+        ps.sort(x, a.pivot)
+        torch.cuda.synchronize()
+        base_lat.append(time.perf_counter() - t0 - req[0])
+    base_span = time.perf_counter() - t0
+    base_keys = sum(r[1] for r in trace[:nb])
+    base_lat.sort()
+    pct = lambda v, q: 1e3 * v[min(len(v) - 1, int(q * len(v)))]
+    line = {
+        "metric": "served keys/s with p50/p99 latency", "value": keys / span, "unit": "keys/s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * span, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "mixed (int32, int64, float32, float64)",
+        "data": "synthetic (SplitMix64 pools, seeded Poisson trace)",
+        "config": {"workload": "served: Poisson %.0f req/s for %.1f s, lengths floor(2^U) U~U[10,26], "
+                               "dtype x distribution uniform, %s splitting, budget %.0f GB"
+                               % (a.rate, a.duration, a.pivot, a.budget_gb),
+                   "requests": len(trace), "keys": keys},
+        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": 1e3 * lat[-1]},
+        "failed_requests": bad,
+        "serial_per_request_ps_sort": {"requests": nb, "keys_per_s": base_keys / base_span,
+                                       "latency_ms": {"p50": pct(base_lat, 0.5), "p99": pct(base_lat, 0.99)}},
+    }
+    print(json.dumps(line))
+    return 0 if bad == 0 else 1
+
+
 # ------------------------------------------------------------ native arm
 def main():
     a = parse()
@@ -272,6 +421,8 @@ def main():
         return run_reference(a)
     if a.workload == "batch":
         return run_batch(a)
+    if a.workload == "serve":
+        return run_serve(a)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
