@@ -491,6 +491,46 @@ __device__ void merge_pieces(const S& s, const int* off, int P, int n)
     }
 }
 
+// Aligned levels: like merge_pieces, but every piece boundary off[0..P] is a
+// multiple of E (the pieces were padded with copies of the largest key), so
+// every merge unit starts and ends on a thread boundary and each thread runs
+// the plain two-way merge of its unit.  The padding sorts last; since a pad
+// equals the largest key bit for bit, the first n - (padding) outputs are the
+// real keys in order.
+template <int NT, int E, typename S>
+__device__ void merge_pieces_aligned(const S& s, const int* off, int P, int n)
+{
+    using V = typename S::V;
+    const int pos0 = threadIdx.x * E;
+    const bool act = pos0 < n;
+    int p0 = 0;  // last piece starting at or before pos0
+    if (act) {
+        int hi = P - 1;
+        while (p0 < hi) {
+            const int mid = (p0 + hi + 1) >> 1;
+            if (off[mid] <= pos0) p0 = mid;
+            else hi = mid - 1;
+        }
+    }
+    for (int sh = 1; (1 << (sh - 1)) < P; sh++) {
+        const int w = 1 << (sh - 1);
+        V out[E];
+        if (act) {
+            const int u = p0 >> sh;
+            const int us = off[min(u * 2 * w, P)], um = off[min(u * 2 * w + w, P)];
+            const int ue = off[min(u * 2 * w + 2 * w, P)];
+            const int x = merge_path(s, us, um, ue, pos0 - us);
+            serial_merge<E, false>(s, us + x, um, um + (pos0 - us - x), ue, E, out);
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < E; i++) s.st(pos0 + i, out[i]);
+        }
+        __syncthreads();
+    }
+}
+
 // Number of elements of the sorted range src[lo, hi) that are < v (lower
 // bound, STRICT = true) or <= v (upper bound, STRICT = false).
 template <bool STRICT, typename K>
@@ -702,6 +742,14 @@ __global__ void __launch_bounds__(NT) k_chunk_plan(Level L, int64_t cnom, int64_
     if (threadIdx.x == 0) choff[G] = carry;
 }
 
+// floor(a * b / c) for non-negative operands; 64-bit arithmetic when the
+// product fits (the common case), 128-bit otherwise.
+__device__ __forceinline__ int64_t muldiv(int64_t a, int64_t b, int64_t c)
+{
+    if (a < (1ll << 31) && b < (1ll << 31)) return (a * b) / c;
+    return (int64_t)(((unsigned __int128)a * (uint64_t)b) / (uint64_t)c);
+}
+
 template <typename K> struct Splitter {
     K key;
     uint32_t run;
@@ -813,11 +861,11 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
             // satisfy j >= (cb + adj + 1) * J / M
             int64_t j = 1;
             if (cb > 0) {
-                j = (int64_t)(((unsigned __int128)(cb + adj + 1) * (uint64_t)J) / (uint64_t)M) - 1;
+                j = muldiv(cb + adj + 1, J, M) - 1;
                 if (j < 1) j = 1;
             }
             for (; j < J; j++) {
-                int64_t t = (int64_t)(((unsigned __int128)j * (uint64_t)M) / (uint64_t)J) - adj;
+                int64_t t = muldiv(j, M, J) - adj;
                 if (t < 1) t = 1;
                 if (t > ci) break;
                 if (t > cb) spl[c0 + j] = Splitter<K>{e.key, (uint32_t)x, (uint32_t)q};
@@ -986,10 +1034,14 @@ __device__ void exact_corank(const GBuf<K>& src, const int64_t* a, const int64_t
 // a split) are appended to `big` and left to the BIG = true launch, which cuts
 // each into exact sub-chunks (exact_corank) and merges those one after another.
 // Output keys pass through the inverse transform XF.
-template <int NT, int E, typename K, int XF, bool BIG>
-__global__ void __launch_bounds__(NT) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
+// ALIGNED (non-BIG only): pieces are padded to multiples of E in shared
+// memory and merged by merge_pieces_aligned; a group whose padded size
+// exceeds the capacity goes to the BIG launch like an oversized one.
+template <int NT, int E, typename K, int XF, bool BIG, bool ALIGNED>
+__global__ void __launch_bounds__(NT, (!BIG && NT <= 512) ? 2 : 1) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
                                               unsigned long long* nbig)
 {
+    static_assert(!(BIG && ALIGNED), "the oversized-group path merges unpadded pieces");
     constexpr int CAP = NT * E;
     extern __shared__ __align__(16) char smem[];
     const int Kr = C.K;
@@ -1035,15 +1087,23 @@ __global__ void __launch_bounds__(NT) k_merge(Level C, GBuf<K> src, GBuf<K> dst,
                 for (int r = threadIdx.x; r < Kr; r += NT) len[r] = (int)(x[r] - a[r]);
                 __syncthreads();
             }
+            auto slot = [](int l) { return ALIGNED ? (l + E - 1) & ~(E - 1) : l; };
             int64_t mine = 0;
-            for (int r = r0; r < r0 + per && r < Kr; r++) mine += len[r];
+            for (int r = r0; r < r0 + per && r < Kr; r++) mine += slot(len[r]);
             int64_t tot;
             int64_t ex = block_exscan<NT>(mine, &tot);
+            if (ALIGNED && tot > CAP) {  // padded pieces do not fit (uniform over the CTA)
+                if (threadIdx.x == 0) {
+                    const unsigned long long q = atomicAdd(nbig, 1ull);
+                    if (PS_IN(q, C.cap, 32) && q < (unsigned long long)C.cap) big[q] = c;
+                }
+                break;
+            }
             for (int r = r0; r < r0 + per && r < Kr; r++) {
                 off[r] = (int)ex;
-                ex += len[r];
+                ex += slot(len[r]);
             }
-            if (threadIdx.x == 0) off[Kr] = (int)take;
+            if (threadIdx.x == 0) off[Kr] = (int)(ALIGNED ? tot : take);
             __syncthreads();
             // one warp per run: coalesced copies of the pieces into shared memory
             const int lane = threadIdx.x & 31;
@@ -1051,10 +1111,12 @@ __global__ void __launch_bounds__(NT) k_merge(Level C, GBuf<K> src, GBuf<K> dst,
                 const int64_t s0 = a[r];
                 const int n_r = len[r], o = off[r];
                 for (int i = lane; i < n_r; i += 32) cp_elem(sb, o + i, src, s0 + i);
+                if (ALIGNED && lane < slot(n_r) - n_r) sb.st(o + n_r + lane, KT<K>::maxkey());
             }
             cp_async_wait_all();
             __syncthreads();
-            merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
+            if (ALIGNED) merge_pieces_aligned<NT, E>(SKeys<K>{sb}, off, Kr, (int)tot);
+            else merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
             for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
             out += take;
             M -= take;

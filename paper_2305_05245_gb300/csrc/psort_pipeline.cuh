@@ -67,9 +67,18 @@ template <typename K> struct Plan {
     // workspace byte offsets
     size_t o_data, o_split, o_off, o_piv, o_c, o_samp, o_merge, total;
 
-    // final chunks aim at 85% of the capacity (splitters land within about
-    // 10% of their targets); oversized ones take the slow exact path
-    static int64_t cnom() { return CAP * 85 / 100; }
+    // Chunks of a fan-in K merge are merged with their pieces padded to
+    // multiples of ME (aligned merge) while K*(ME-1), the worst-case padding,
+    // stays within a quarter of the capacity.
+    static bool aligned(int64_t K_) { return K_ * (Cfg<K>::ME - 1) * 4 <= CAP; }
+    // chunks aim at 85% of the capacity left after the average padding
+    // (splitters land within about 10% of their targets); oversized ones take
+    // the slow exact path
+    static int64_t cnom(int64_t K_)
+    {
+        const int64_t room = aligned(K_) ? CAP - K_ * (Cfg<K>::ME - 1) / 2 : CAP;
+        return room * 85 / 100;
+    }
     static int64_t jcap(int64_t K_) { return std::max<int64_t>(1, (POOL / 2 - K_) / 2); }
     // children per refinement level: the pool takes about max(2K, 96) samples
     // per child, so J is capped near POOL/max(2K, 96)
@@ -86,13 +95,13 @@ template <typename K> struct Plan {
         m.K = K_;
         m.jcap = jcap(K_);
         const int64_t jl = jlevel(K_);
-        int64_t need = (Mmax + cnom() - 1) / cnom();
+        int64_t need = (Mmax + cnom(K_) - 1) / cnom(K_);
         m.nlev = 0;
         if (jl >= 2)
             for (int64_t x = need; x > 1 && m.nlev < MAXLEV; x = (x + jl - 1) / jl) m.nlev++;
         m.G[0] = G0;
         for (int l = 0; l < m.nlev; l++) {
-            int64_t c = cnom();
+            int64_t c = cnom(K_);
             for (int q = 0; q < m.nlev - 1 - l; q++) c *= jl;
             m.cnom[l] = c;
             m.G[l + 1] = Nsum / c + m.G[l] + 1;
@@ -305,13 +314,13 @@ template <typename K> struct Pipeline {
         if ((e = cudaMemsetAsync(nbig, 0, 8, s)) != cudaSuccess) return e;
         const Level& Lf = Lv[sh.nlev];
         const int64_t gf = sh.G[sh.nlev];
-        auto fm = k_merge<MNT, ME, K, XF, false>;
+        auto fm = Plan<K>::aligned(Kr) ? k_merge<MNT, ME, K, XF, false, true> : k_merge<MNT, ME, K, XF, false, false>;
         if ((e = smem_attr(fm, merge_smem(Kr))) != cudaSuccess) return e;
         {
             ProfScope ps_(fin ? "merge_final" : "merge_inblock", s);
             fm<<<(unsigned)gf, MNT, merge_smem(Kr), s>>>(Lf, src, dst, pl.N, big + 1, nbig);
         }
-        auto fb = k_merge<MNT, BE, K, XF, true>;
+        auto fb = k_merge<MNT, BE, K, XF, true, false>;
         if ((e = smem_attr(fb, big_smem(Kr))) != cudaSuccess) return e;
         {
             ProfScope ps_(fin ? "merge_big_final" : "merge_big_inblock", s);
