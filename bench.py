@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=1 << 30)
+    ap.add_argument("--n", type=int, default=None, help="keys (default 2^30; table1: 10^8)")
     ap.add_argument("--dtype", default="int64", choices=sorted(BYTES))
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--pivot", default="exact", choices=["exact", "regular"])
@@ -48,14 +48,17 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "table1"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=32.0, help="serve: admission budget")
     ap.add_argument("--segments", type=int, default=20000)
     ap.add_argument("--baseline-segments", type=int, default=2000,
                     help="segments timed with one ps_sort call each (batch workload)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.n is None and a.workload != "table1":
+        a.n = 1 << 30
+    return a
 
 
 def workload_name(a) -> str:
@@ -268,6 +271,108 @@ def run_batch(a):
     return 0 if ok else 1
 
 
+# ------------------------------------------------------------ Table 1 inputs
+def table1_inputs(n: int, dev):
+    """The paper's six Table 1 inputs at N elements (seeded, synthetic):
+    (name, tensor, kind, dtype code) with kind "keys" or "struct"."""
+    import numpy as np
+    import torch
+    import synth
+
+    def host_u32(dist):
+        return torch.from_numpy(synth.keys(n, "uint32", dist, seed=synth.seed_for("t1", dist, n)).view(np.int32)).to(dev)
+    out = [("UniformInt", synth.keys_torch(n, "uint32", "uniform", seed=synth.seed_for("t1", "ui", n), device=dev),
+            "keys", 4),
+           ("UniformFloat", synth.keys_torch(n, "float32", "uniform", seed=synth.seed_for("t1", "uf", n), device=dev),
+            "keys", 2),
+           ("AlmostSorted", host_u32("almost_sorted"), "keys", 4),
+           ("Duplicate3", host_u32("three_valued"), "keys", 4)]
+    pair = torch.empty((n, 2), dtype=torch.int64, device=dev)
+    pair[:, 0] = synth.splitmix64_torch(synth.seed_for("t1", "pair", n), n, dev)
+    pair[:, 1] = torch.arange(n, device=dev)
+    out.append(("Pair", pair, "struct", 0))
+    g = torch.Generator(device=dev).manual_seed(synth.seed_for("t1", "particle", n) & 0x7FFFFFFF)
+    part = torch.empty((n, 12), dtype=torch.int64, device=dev)
+    part[:, 0] = synth.splitmix64_torch(synth.seed_for("t1", "particle-key", n), n, dev)
+    part[:, 1:] = torch.rand((n, 11), dtype=torch.float64, device=dev, generator=g).view(torch.int64)
+    out.append(("Particle", part, "struct", 0))
+    return out
+
+
+def run_table1(a):
+    """NEXT-4: the paper's Table 1 inputs (UniformInt, UniformFloat,
+    AlmostSorted, Duplicate3: 4-byte keys; Pair: 16-byte, Particle: 96-byte
+    records sorted by a uint64 key) at N = 10^8, both pivot modes, with the
+    partition imbalance (largest partition / (N / n_P)) of the keys-only sorts."""
+    import ctypes
+    import numpy as np
+    import torch
+
+    import paper_2305_05245_gb300 as ps
+    from paper_2305_05245_gb300 import _lib
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    n = a.n or 100_000_000
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+    rows, ok = [], True
+    for name, pristine, kind, code in table1_inputs(n, dev):
+        for mode in ("regular", "exact"):
+            x = pristine.clone()
+
+            def once():
+                if kind == "struct":
+                    ps.sort_struct(x, pivot_mode=mode)
+                else:
+                    _lib.check(lib, "ps_sort", lib.ps_sort(x.data_ptr(), n, code, ps._mode(mode),
+                                                          ps._stream_handle(None)))
+            for _ in range(a.warmup):
+                x.copy_(pristine)
+                once()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(a.steps)]
+            for i in range(a.steps):
+                x.copy_(pristine)
+                evs[i][0].record(stream)
+                once()
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+            if kind == "struct":
+                k = x[:, 0] ^ (-(1 << 63))
+                good = bool((k[1:] >= k[:-1]).all()) and torch.equal(pristine[x[:, 1]][:, 0], x[:, 0]) \
+                    if name == "Pair" else bool((k[1:] >= k[:-1]).all())
+                imb = None
+            else:
+                kk = x.to(torch.int64) & 0xFFFFFFFF if code == 4 else x
+                good = bool((kk[1:] >= kk[:-1]).all())
+                nb, np_ = ps.resolve_params(n, code)
+                tr, ct = ps._make_trace(n, code, nb, np_, x.dtype, dev, False)
+                x.copy_(pristine)
+                rc = lib.ps_sort_ex(x.data_ptr(), n, code, ps._mode(mode), ctypes.byref(ps._params(nb, np_)),
+                                    ctypes.byref(ct), ps._stream_handle(None))
+                _lib.check(lib, "ps_sort_ex", rc)
+                torch.cuda.synchronize()
+                sizes = torch.diff(tr.offsets[: np_ + 1])
+                imb = float(sizes.max()) / (n / np_)
+            ok = ok and good
+            rows.append({"input": name, "pivot": mode, "ms": ms, "Melem_per_s": n / ms / 1e3,
+                         "record_bytes": int(pristine.element_size() * (pristine.shape[1] if pristine.dim() == 2 else 1)),
+                         "max_partition_over_mean": imb, "check": "ok" if good else "FAILED"})
+            del x
+    geo = float(np.exp(np.mean([np.log(r["Melem_per_s"]) for r in rows]))) if rows else 0.0
+    line = {
+        "metric": "Table 1 inputs: elements/s per input and pivot mode (geometric mean)", "value": geo * 1e6,
+        "unit": "elements/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32 keys; u64-keyed 16 B and 96 B records",
+        "data": "synthetic (SplitMix64 keys, seeded), resident in HBM",
+        "config": {"workload": "Table 1 inputs at N=%d, automatic n_B/n_P" % n, "n": n},
+        "table": rows, "check": "ok" if ok else "FAILED",
+    }
+    print(json.dumps(line))
+    return 0 if ok else 1
+
+
 # ------------------------------------------------------------ served workload
 SERVE_DTYPES = ["int32", "int64", "float32", "float64"]
 SERVE_DISTS = ["uniform", "sorted", "reverse", "few_unique", "gaussian"]
@@ -423,6 +528,8 @@ def main():
         return run_batch(a)
     if a.workload == "serve":
         return run_serve(a)
+    if a.workload == "table1":
+        return run_table1(a)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -114,6 +114,24 @@ int ps_sort_ex(void* keys, int64_t n, int dtype, int pivot_mode, const ps_params
 int ps_sort_pairs(uint64_t* keys, uint32_t* payload, int64_t n, int pivot_mode,
                   const ps_params* params, const ps_trace* trace, ps_stream_t stream);
 
+/* Sort n fixed-size records in place by the uint64 key stored inside each
+ * record (Table 1's "Pair", 16 B = key + index, and "Particle", 96 B = key +
+ * 88 B of particle data, both "sorted by the key (uint64_t)").
+ *   records       n * record_bytes bytes of device memory, array of
+ *                 structures, 8-byte aligned
+ *   record_bytes  multiple of 8, 8 .. PS_STRUCT_MAX_BYTES
+ *   key_offset    byte offset of the key inside a record: multiple of 8,
+ *                 at most record_bytes - 8; the key is read as unsigned
+ * Records with equal keys keep their input order (the order is (key, input
+ * position)), so the result is unique.  n must be below 2^32.  The four steps
+ * run on (key, position) pairs (as ps_sort_pairs); the records then move once,
+ * by a gather.  Workspace from the pool: n * record_bytes bytes for a copy of
+ * the records plus 12 * n bytes of pairs and the pair sort's own.  Argument
+ * errors return PS_ERR_INVALID_ARG before anything is queued. */
+#define PS_STRUCT_MAX_BYTES 4096
+int ps_sort_struct(void* records, int64_t n, int64_t record_bytes, int64_t key_offset, int pivot_mode,
+                   const ps_params* params, ps_stream_t stream);
+
 /* Sort many independent segments of one key array in place: segment i is
  * keys[seg_offsets[i], seg_offsets[i+1]) (seg_offsets: n_segs+1 non-decreasing
  * DEVICE int64 offsets).  Segments are binned by length; every bin runs the

@@ -18,7 +18,7 @@ from ._lib import PS_PIVOT_EXACT, PS_PIVOT_REGULAR, PsortError  # noqa: F401
 
 __all__ = ["sort", "sort_pairs", "sort_host", "resolve_params", "workspace_bytes", "Trace",
            "PsortError", "PS_PIVOT_EXACT", "PS_PIVOT_REGULAR", "profile_enable", "profile_read",
-           "profile_reset", "sort_noalloc", "sort_batch", "Server"]
+           "profile_reset", "sort_noalloc", "sort_batch", "sort_struct", "Server"]
 
 _MODES = {"regular": _lib.PS_PIVOT_REGULAR, "psrs": _lib.PS_PIVOT_REGULAR, 0: 0,
           "exact": _lib.PS_PIVOT_EXACT, "pses": _lib.PS_PIVOT_EXACT, 1: 1}
@@ -153,6 +153,28 @@ def sort_pairs(keys, payload, pivot_mode="exact", n_blocks: int = 0, n_parts: in
                            ctypes.byref(ct) if ct is not None else None, _stream_handle(stream))
     _lib.check(lib, "ps_sort_pairs", rc)
     return tr
+
+
+def sort_struct(records, record_bytes: int | None = None, key_offset: int = 0, pivot_mode="exact",
+                n_blocks: int = 0, n_parts: int = 0, stream=None) -> None:
+    """Sort fixed-size records in place by the uint64 key at byte
+    ``key_offset`` of each record (ps_sort_struct); equal keys keep their
+    input order.  ``records`` is a contiguous CUDA tensor; ``record_bytes``
+    defaults to the byte size of one row of a 2-D tensor."""
+    lib = _lib.load()
+    if not records.is_cuda or not records.is_contiguous():
+        raise ValueError("records must be a contiguous CUDA tensor")
+    nbytes = records.numel() * records.element_size()
+    if record_bytes is None:
+        if records.dim() != 2:
+            raise ValueError("record_bytes is needed unless records is 2-D (one row per record)")
+        record_bytes = records.shape[1] * records.element_size()
+    if record_bytes <= 0 or nbytes % record_bytes:
+        raise ValueError("the tensor is not a whole number of records")
+    n = nbytes // record_bytes
+    rc = lib.ps_sort_struct(records.data_ptr() if n else None, n, record_bytes, key_offset, _mode(pivot_mode),
+                            ctypes.byref(_params(n_blocks, n_parts)), _stream_handle(stream))
+    _lib.check(lib, "ps_sort_struct", rc)
 
 
 def sort_host(arr, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, stream=None) -> None:

@@ -17,7 +17,7 @@ LIB_CHECKED = os.path.join(HERE, "libpsort_checked.so")
 BUILD = os.path.join(HERE, "_build")
 
 SOURCES = ["psort_u32.cu", "psort_u64.cu", "psort_rec.cu", "psort_api.cu", "psort_noalloc.cu",
-           "psort_server.cu"]
+           "psort_server.cu", "psort_struct.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

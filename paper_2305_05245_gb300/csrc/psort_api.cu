@@ -192,6 +192,11 @@ static int sort_common(void* keys, uint32_t* payload, int64_t n, int dtype, int 
     return dispatch(a);
 }
 
+int sort_records(uint64_t* keys, uint32_t* payload, int64_t n, int mode, const ps_params* params, cudaStream_t s)
+{
+    return sort_common(keys, payload, n, -1, mode, params, nullptr, s);
+}
+
 static size_t dtype_size(int dtype)
 {
     return (dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32) ? 4 : 8;
@@ -325,6 +330,20 @@ int ps_sort_pairs(uint64_t* keys, uint32_t* payload, int64_t n, int pivot_mode, 
                   const ps_trace* trace, ps_stream_t stream)
 {
     return sort_common(keys, payload, n, -1, pivot_mode, params, trace, stream);
+}
+
+int ps_sort_struct(void* records, int64_t n, int64_t record_bytes, int64_t key_offset, int pivot_mode,
+                   const ps_params* params, ps_stream_t stream)
+{
+    if (n < 0 || n >= (int64_t(1) << 32)) return PS_ERR_INVALID_ARG;
+    if (record_bytes < 8 || record_bytes > PS_STRUCT_MAX_BYTES || record_bytes % 8 != 0) return PS_ERR_INVALID_ARG;
+    if (key_offset < 0 || key_offset % 8 != 0 || key_offset > record_bytes - 8) return PS_ERR_INVALID_ARG;
+    if (pivot_mode != PS_PIVOT_REGULAR && pivot_mode != PS_PIVOT_EXACT) return PS_ERR_UNSUPPORTED;
+    const int rc = check_params(params);
+    if (rc != PS_OK) return rc;
+    if (n <= 1) return PS_OK;
+    if (!records || (uintptr_t)records % 8 != 0) return PS_ERR_INVALID_ARG;
+    return struct_sort(records, n, record_bytes, key_offset, pivot_mode, params, (cudaStream_t)stream);
 }
 
 int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dtype, int pivot_mode,

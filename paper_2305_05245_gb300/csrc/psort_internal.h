@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstddef>
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 #include <cuda_runtime.h>
@@ -68,6 +69,11 @@ int viol_read_rec(unsigned long long* out);
 // instance table; when given, the call does not wait for the stream.
 int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
                int64_t* pinned, size_t pinned_cap);
+// Records (uint64 key, uint32 payload) through the validated record path.
+int sort_records(uint64_t* keys, uint32_t* payload, int64_t n, int mode, const ps_params* params, cudaStream_t s);
+// Fixed-size records sorted by an embedded uint64 key (arguments validated).
+int struct_sort(void* records, int64_t n, int64_t rb, int64_t ko, int mode, const ps_params* params,
+                cudaStream_t s);
 // Workspace bytes of a single sort of n keys with automatic parameters.
 size_t sort_ws_bytes(int64_t n, int dtype);
 // The same sorts on a caller-provided workspace (allocation-free entry point).

@@ -57,6 +57,18 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ps_sort(None, 10, 0, 0, None) == -1
     assert lib.ps_sort(ctypes.c_void_p(0x1002), 10, 1, 0, None) == -1
     assert lib.ps_sort_pairs(ctypes.c_void_p(0x1000), None, 10, 0, None, None, None) == -1
+    # records sorted by an embedded key: size, record size, key offset, mode, alignment
+    assert lib.ps_sort_struct(None, -1, 16, 0, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 1 << 32, 16, 0, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 10, 12, 0, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 10, 0, 0, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 10, _lib.PS_STRUCT_MAX_BYTES + 8, 0, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 10, 16, 4, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 10, 16, 16, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 10, 16, 8, 5, None, None) == -2
+    assert lib.ps_sort_struct(None, 10, 16, 8, 1, None, None) == -1
+    assert lib.ps_sort_struct(ctypes.c_void_p(0x1004), 10, 16, 8, 1, None, None) == -1
+    assert lib.ps_sort_struct(None, 1, 96, 0, 0, None, None) == 0
     # n = 0 and n = 1 are no-ops
     assert lib.ps_sort(None, 0, 0, 0, None) == 0
     assert lib.ps_sort(None, 1, 3, 1, None) == 0
