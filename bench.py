@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "table1"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "table1", "merge_ablation"])
+    ap.add_argument("--merge-variant", default="tree", choices=["tree", "sort", "select"],
+                    help="step 4 chunk merge (single workload)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=32.0, help="serve: admission budget")
@@ -56,7 +58,7 @@ def parse():
     ap.add_argument("--baseline-segments", type=int, default=2000,
                     help="segments timed with one ps_sort call each (batch workload)")
     a = ap.parse_args()
-    if a.n is None and a.workload != "table1":
+    if a.n is None and a.workload not in ("table1", "merge_ablation"):
         a.n = 1 << 30
     return a
 
@@ -373,6 +375,76 @@ def run_table1(a):
     return 0 if ok else 1
 
 
+def run_merge_ablation(a):
+    """NEXT-3: step 4 with each chunk-merge variant (pairwise merge levels,
+    copy and sort, selection tree) on the Table 1 key inputs at N = 10^8 with
+    exact splitting, as the paper compares merging algorithms for PSES."""
+    import numpy as np
+    import torch
+
+    import paper_2305_05245_gb300 as ps
+    from paper_2305_05245_gb300 import _lib
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    n = a.n or 100_000_000
+    lib = _lib.load()
+    import ctypes
+    stream = torch.cuda.current_stream()
+    rows, ok = [], True
+    inputs = [t for t in table1_inputs(n, dev) if t[2] == "keys"]
+    inputs.append(("UniformInt64", synth_keys_torch(n, "int64", "uniform", dev), "keys", 1))
+    for name, pristine, _, code in inputs:
+        ref = None
+        for variant in ("tree", "sort", "select"):
+            x = pristine.clone()
+            prm = ps._params(0, 0, variant)
+
+            def once():
+                _lib.check(lib, "ps_sort_ex", lib.ps_sort_ex(x.data_ptr(), n, code, ps._mode(a.pivot),
+                                                              ctypes.byref(prm), None, ps._stream_handle(None)))
+            for _ in range(a.warmup):
+                x.copy_(pristine)
+                once()
+            torch.cuda.synchronize()
+            ps.profile_reset()
+            ps.profile_enable(True)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(a.steps)]
+            for i in range(a.steps):
+                x.copy_(pristine)
+                evs[i][0].record(stream)
+                once()
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+            ps.profile_enable(False)
+            prof = ps.profile_read()
+            ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+            if ref is None:
+                ref = x.clone()
+            good = torch.equal(ref, x)
+            ok = ok and good
+            rows.append({"input": name, "merge_variant": variant, "ms": ms,
+                         "merge_final_ms": prof.get("merge_final", (0, 0.0))[1] / a.steps,
+                         "check": "ok" if good else "FAILED"})
+            del x
+    line = {
+        "metric": "step-4 merge variants: sort time and final-merge time per input", "value": None,
+        "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32/int64 keys",
+        "data": "synthetic (SplitMix64 keys, seeded), resident in HBM",
+        "config": {"workload": "merge variants on Table 1 key inputs at N=%d, %s splitting, automatic n_B/n_P"
+                               % (n, a.pivot), "n": n},
+        "table": rows, "check": "ok" if ok else "FAILED",
+    }
+    print(json.dumps(line))
+    return 0 if ok else 1
+
+
+def synth_keys_torch(n, dtype, dist, dev):
+    import synth
+    return synth.keys_torch(n, dtype, dist, seed=synth.seed_for("ablation", dtype, dist, n), device=dev)
+
+
 # ------------------------------------------------------------ served workload
 SERVE_DTYPES = ["int32", "int64", "float32", "float64"]
 SERVE_DISTS = ["uniform", "sorted", "reverse", "few_unique", "gaussian"]
@@ -530,6 +602,8 @@ def main():
         return run_serve(a)
     if a.workload == "table1":
         return run_table1(a)
+    if a.workload == "merge_ablation":
+        return run_merge_ablation(a)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -568,7 +642,7 @@ def main():
                                     "uint32": 4, "uint64": 5}[a.dtype], a.n_blocks, a.n_parts)
 
     def step():
-        ps.sort(keys, a.pivot, n_blocks=a.n_blocks, n_parts=a.n_parts)
+        ps.sort(keys, a.pivot, n_blocks=a.n_blocks, n_parts=a.n_parts, merge_variant=a.merge_variant)
 
     for _ in range(a.warmup):
         keys.copy_(pristine)

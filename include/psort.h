@@ -75,8 +75,23 @@ typedef enum {
 typedef struct {
     int64_t n_blocks;
     int64_t n_parts;
-    int64_t reserved[2]; /* must be 0 */
+    int64_t merge_variant; /* step 4 (Sec. 2.2), one of ps_merge_variant */
+    int64_t reserved;      /* must be 0 */
 } ps_params;
+
+/* How step 4 merges the pieces of one chunk of a partition (Sec. 2.2 and the
+ * comparison of multiway merging algorithms in Sec. 4).  All three give the
+ * same output; the default is the fast one, the others are for comparison.
+ *   PS_MERGE_TREE  0: the pieces are merged pairwise, level by level
+ *                     (ceil(log2 n_B) merge-path levels in shared memory)
+ *   PS_MERGE_SORT  1: the pieces are copied next to each other and the chunk
+ *                     is sorted as a whole (Sec. 2.2, "copying them into an
+ *                     output array and sorting it")
+ *   PS_MERGE_SELECT 2: one thread per chunk pops the chunk's smallest head
+ *                     from a selection (loser) tree over the n_B run heads
+ *                     (Sec. 2.2, Knuth's selection tree), reading the runs
+ *                     straight from device memory */
+typedef enum { PS_MERGE_TREE = 0, PS_MERGE_SORT = 1, PS_MERGE_SELECT = 2 } ps_merge_variant;
 
 /* Optional record of the method's intermediates, for checking.  Each pointer
  * may be NULL (that intermediate is not reported).  All are device pointers

@@ -51,10 +51,16 @@ def _mode(m) -> int:
         raise ValueError("pivot mode must be 'regular' or 'exact'") from None
 
 
-def _params(n_blocks: int, n_parts: int):
+_MERGES = {"tree": 0, "sort": 1, "select": 2, 0: 0, 1: 1, 2: 2}
+
+
+def _params(n_blocks: int, n_parts: int, merge_variant="tree"):
     p = _lib.PsParams()
     p.n_blocks = n_blocks
     p.n_parts = n_parts
+    if merge_variant not in _MERGES:
+        raise ValueError("merge_variant must be 'tree', 'sort' or 'select'")
+    p.merge_variant = _MERGES[merge_variant]
     return p
 
 
@@ -116,9 +122,12 @@ def _make_trace(n: int, code: int, n_blocks: int, n_parts: int, key_dtype, devic
 
 
 def sort(keys, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, trace: bool = False,
-         stream=None):
+         stream=None, merge_variant="tree"):
     """Sort a contiguous 1-D CUDA tensor in place (int32, int64, float32,
-    float64, uint32, uint64).  Returns a Trace when ``trace`` is true."""
+    float64, uint32, uint64).  Returns a Trace when ``trace`` is true.
+    ``merge_variant`` picks step 4's chunk merge: "tree" (pairwise merge
+    levels, the default), "sort" (copy the pieces and sort) or "select"
+    (one selection tree per chunk); all give the same result."""
     lib = _lib.load()
     if not keys.is_cuda or keys.dim() != 1 or not keys.is_contiguous():
         raise ValueError("keys must be a contiguous 1-D CUDA tensor")
@@ -128,14 +137,14 @@ def sort(keys, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, trace: b
     if trace:
         tr, ct = _make_trace(n, code, n_blocks, n_parts, keys.dtype, keys.device, False)
     rc = lib.ps_sort_ex(keys.data_ptr() if n else None, n, code, _mode(pivot_mode),
-                        ctypes.byref(_params(n_blocks, n_parts)),
+                        ctypes.byref(_params(n_blocks, n_parts, merge_variant)),
                         ctypes.byref(ct) if ct is not None else None, _stream_handle(stream))
     _lib.check(lib, "ps_sort_ex", rc)
     return tr
 
 
 def sort_pairs(keys, payload, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0,
-               trace: bool = False, stream=None):
+               trace: bool = False, stream=None, merge_variant="tree"):
     """Sort records in place by (key, payload): ``keys`` a contiguous 1-D CUDA
     tensor of 64-bit keys (int64 storage read as unsigned), ``payload`` one of
     32-bit payloads (int32 storage read as unsigned)."""
@@ -149,7 +158,7 @@ def sort_pairs(keys, payload, pivot_mode="exact", n_blocks: int = 0, n_parts: in
     if trace:
         tr, ct = _make_trace(n, -1, n_blocks, n_parts, keys.dtype, keys.device, True)
     rc = lib.ps_sort_pairs(keys.data_ptr() if n else None, payload.data_ptr() if n else None, n,
-                           _mode(pivot_mode), ctypes.byref(_params(n_blocks, n_parts)),
+                           _mode(pivot_mode), ctypes.byref(_params(n_blocks, n_parts, merge_variant)),
                            ctypes.byref(ct) if ct is not None else None, _stream_handle(stream))
     _lib.check(lib, "ps_sort_pairs", rc)
     return tr

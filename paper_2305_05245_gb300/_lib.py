@@ -30,7 +30,7 @@ PS_STRUCT_MAX_BYTES = 4096
 
 class PsParams(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int64), ("n_parts", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 2)]
+                ("merge_variant", ctypes.c_int64), ("reserved", ctypes.c_int64)]
 
 
 class PsTrace(ctypes.Structure):

@@ -151,7 +151,8 @@ static int check_params(const ps_params* p)
     if (!p) return PS_OK;
     if (p->n_blocks < 0 || p->n_blocks > MAX_BLOCKS) return PS_ERR_INVALID_ARG;
     if (p->n_parts < 0 || p->n_parts > MAX_PARTS) return PS_ERR_INVALID_ARG;
-    if (p->reserved[0] != 0 || p->reserved[1] != 0) return PS_ERR_INVALID_ARG;
+    if (p->merge_variant < PS_MERGE_TREE || p->merge_variant > PS_MERGE_SELECT) return PS_ERR_INVALID_ARG;
+    if (p->reserved != 0) return PS_ERR_INVALID_ARG;
     return PS_OK;
 }
 
@@ -187,6 +188,7 @@ static int sort_common(void* keys, uint32_t* payload, int64_t n, int dtype, int 
     a.mode = mode;
     a.n_B = r.n_blocks;
     a.n_P = r.n_parts;
+    a.merge_variant = (int)r.merge_variant;
     a.trace = trace;
     a.stream = (cudaStream_t)stream;
     return dispatch(a);

@@ -20,6 +20,7 @@ struct SortArgs {
     int dtype;           // ps_dtype, or -1 for records
     int mode;            // ps_pivot_mode
     int64_t n_B, n_P;    // resolved
+    int merge_variant = 0;  // ps_merge_variant of step 4
     const ps_trace* trace;
     cudaStream_t stream;
     // Batched sorts: n_inst independent instances sharing n_B and n_P, with

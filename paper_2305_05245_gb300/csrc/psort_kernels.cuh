@@ -1037,11 +1037,15 @@ __device__ void exact_corank(const GBuf<K>& src, const int64_t* a, const int64_t
 // ALIGNED (non-BIG only): pieces are padded to multiples of E in shared
 // memory and merged by merge_pieces_aligned; a group whose padded size
 // exceeds the capacity goes to the BIG launch like an oversized one.
-template <int NT, int E, typename K, int XF, bool BIG, bool ALIGNED>
+// SORTCHUNK (non-BIG only): the pieces are copied side by side and the chunk
+// is sorted as a whole, ignoring that the pieces are sorted (the "copy and
+// sort" way of multiway merging, Sec. 2.2).
+template <int NT, int E, typename K, int XF, bool BIG, bool ALIGNED, bool SORTCHUNK = false>
 __global__ void __launch_bounds__(NT, (!BIG && NT <= 512) ? 2 : 1) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
                                               unsigned long long* nbig)
 {
     static_assert(!(BIG && ALIGNED), "the oversized-group path merges unpadded pieces");
+    static_assert(!(SORTCHUNK && (BIG || ALIGNED)), "copy-and-sort chunks are unpadded and fit the capacity");
     constexpr int CAP = NT * E;
     extern __shared__ __align__(16) char smem[];
     const int Kr = C.K;
@@ -1115,8 +1119,23 @@ __global__ void __launch_bounds__(NT, (!BIG && NT <= 512) ? 2 : 1) k_merge(Level
             }
             cp_async_wait_all();
             __syncthreads();
-            if (ALIGNED) merge_pieces_aligned<NT, E>(SKeys<K>{sb}, off, Kr, (int)tot);
-            else merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
+            if constexpr (SORTCHUNK) {
+                K r[E];
+#pragma unroll
+                for (int j = 0; j < E; j++) {
+                    const int i = threadIdx.x * E + j;
+                    r[j] = i < (int)take ? sb.ld(i) : KT<K>::maxkey();
+                }
+                reg_sort<E>(r);
+#pragma unroll
+                for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
+                __syncthreads();
+                merge_levels_pow2<NT, E>(SKeys<K>{sb});
+            } else if (ALIGNED) {
+                merge_pieces_aligned<NT, E>(SKeys<K>{sb}, off, Kr, (int)tot);
+            } else {
+                merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
+            }
             for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
             out += take;
             M -= take;
@@ -1125,6 +1144,90 @@ __global__ void __launch_bounds__(NT, (!BIG && NT <= 512) ? 2 : 1) k_merge(Level
                 __syncthreads();
             }
         }
+    }
+}
+
+// Selection-tree merge (Sec. 2.2): one thread merges one whole group of the
+// last level.  Its run heads live in shared memory; a loser tree over KP
+// leaves (KP a power of two >= K; leaves K..KP-1 are empty runs) holds at
+// every inner node the loser of the match played there and at node 0 the
+// overall winner.  Each output takes the winner's head, advances that run
+// (reading device memory) and replays the matches on its leaf-to-root path.
+// Order: non-empty before empty, then key, then run index (ties to the lower
+// block, as the merge of Sec. 2.2 needs no particular tie rule but the
+// output must be unique).  TPB threads per CTA, each with its own tree.
+template <typename K, int XF>
+__global__ void k_merge_select(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int KP, int TPB)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int Kr = C.K;
+    int64_t ng = *C.ng;
+    if (ng > C.cap) ng = C.cap;
+    const int64_t c = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (threadIdx.x >= TPB || c >= ng) return;
+    char* mine = smem + (size_t)threadIdx.x * KP * (sizeof(K) + 2 * sizeof(int64_t) + sizeof(int));
+    K* head = (K*)mine;
+    int64_t* pos = (int64_t*)(head + KP);
+    int64_t* end = pos + KP;
+    int* tree = (int*)(end + KP);
+    const int64_t out0 = C.base[c], M = C.size[c];
+    if (out0 < 0 || M < 0 || out0 + M > nout) return;
+    for (int r = 0; r < KP; r++) {
+        int64_t lo = 0, hi = 0;
+        if (r < Kr) {
+            lo = C.lo[c * Kr + r];
+            hi = C.hi[c * Kr + r];
+        }
+        pos[r] = lo;
+        end[r] = hi > lo ? hi : lo;
+        head[r] = lo < hi ? src.ld(lo) : KT<K>::maxkey();
+        tree[r] = -1;
+    }
+    // r beats q: r is non-empty and q empty, or both non-empty and
+    // (head, run) of r is smaller
+    auto beats = [&](int r, int q) {
+        const bool er = pos[r] >= end[r], eq = pos[q] >= end[q];
+        if (er != eq) return eq;
+        if (er) return r < q;
+        if (key_lt(head[r], head[q])) return true;
+        if (key_lt(head[q], head[r])) return false;
+        return r < q;
+    };
+    // build: leaves enter one by one; the first arrival at an inner node
+    // waits there, the second plays it, the loser stays
+    for (int r = 0; r < KP; r++) {
+        int cand = r;
+        int node = (r + KP) >> 1;
+        bool placed = false;
+        while (node >= 1) {
+            if (tree[node] < 0) {
+                tree[node] = cand;
+                placed = true;
+                break;
+            }
+            if (beats(tree[node], cand)) {
+                const int t = tree[node];
+                tree[node] = cand;
+                cand = t;
+            }
+            node >>= 1;
+        }
+        if (!placed) tree[0] = cand;
+    }
+    for (int64_t i = 0; i < M; i++) {
+        const int w = tree[0];
+        dst.template stx<XF>(out0 + i, head[w]);
+        pos[w]++;
+        if (pos[w] < end[w]) head[w] = src.ld(pos[w]);
+        int cand = w;
+        for (int node = (w + KP) >> 1; node >= 1; node >>= 1) {
+            if (beats(tree[node], cand)) {
+                const int t = tree[node];
+                tree[node] = cand;
+                cand = t;
+            }
+        }
+        tree[0] = cand;
     }
 }
 

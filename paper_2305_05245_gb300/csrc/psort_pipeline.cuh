@@ -262,9 +262,10 @@ template <typename K> struct Pipeline {
     // Multiway merge of every group of `job` from src into dst: level-0 windows,
     // sh.nlev refinement levels (sample pool, co-ranks, child windows), then
     // one CTA per final group.
+    // variant: ps_merge_variant of the last level's chunk merge.
     template <int XF>
     static cudaError_t merge(const MergeJob& job, const MergeShape& sh, GBuf<K> src, GBuf<K> dst,
-                             const Plan<K>& pl, char* ws, cudaStream_t s)
+                             const Plan<K>& pl, char* ws, cudaStream_t s, int variant = PS_MERGE_TREE)
     {
         const bool fin = job.kind == 1;
         char* m = ws + pl.o_merge;
@@ -314,7 +315,21 @@ template <typename K> struct Pipeline {
         if ((e = cudaMemsetAsync(nbig, 0, 8, s)) != cudaSuccess) return e;
         const Level& Lf = Lv[sh.nlev];
         const int64_t gf = sh.G[sh.nlev];
-        auto fm = Plan<K>::aligned(Kr) ? k_merge<MNT, ME, K, XF, false, true> : k_merge<MNT, ME, K, XF, false, false>;
+        if (variant == PS_MERGE_SELECT) {
+            // one thread per group, each with its own selection tree
+            int KP = 1;
+            while (KP < Kr) KP <<= 1;
+            const size_t per = (size_t)KP * (sizeof(K) + 2 * sizeof(int64_t) + sizeof(int));
+            const int tpb = (int)std::max<size_t>(1, std::min<size_t>(32, (size_t)(160 << 10) / per));
+            auto fs = k_merge_select<K, XF>;
+            if ((e = smem_attr(fs, (size_t)tpb * per)) != cudaSuccess) return e;
+            ProfScope ps_(fin ? "merge_final" : "merge_inblock", s);
+            fs<<<(unsigned)((gf + tpb - 1) / tpb), 32, (size_t)tpb * per, s>>>(Lf, src, dst, pl.N, KP, tpb);
+            return cudaGetLastError();
+        }
+        auto fm = variant == PS_MERGE_SORT ? k_merge<MNT, ME, K, XF, false, false, true>
+                  : Plan<K>::aligned(Kr)   ? k_merge<MNT, ME, K, XF, false, true>
+                                           : k_merge<MNT, ME, K, XF, false, false>;
         if ((e = smem_attr(fm, merge_smem(Kr))) != cudaSuccess) return e;
         {
             ProfScope ps_(fin ? "merge_final" : "merge_inblock", s);
@@ -417,7 +432,7 @@ template <typename K> struct Pipeline {
         job.splits = splits;
         job.offsets = offs;
         job.n_P = pl.n_P;
-        if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, user, pl, ws, s)) != cudaSuccess) return e;
+        if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, user, pl, ws, s, a.merge_variant)) != cudaSuccess) return e;
         // Trace (single sorts only).
         if (a.trace && pl.n_inst == 1) {
             const ps_trace* t = a.trace;

@@ -51,7 +51,11 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
     p.n_blocks, p.n_parts = 4, (1 << 20) + 1
     assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
-    p.n_parts, p.reserved[0] = 4, 1
+    p.n_parts, p.reserved = 4, 1
+    assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
+    p.reserved, p.merge_variant = 0, 3
+    assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
+    p.merge_variant = -1
     assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
     # null keys with n >= 2, misaligned keys
     assert lib.ps_sort(None, 10, 0, 0, None) == -1
