@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=None, help="keys (default 2^30; table1: 10^8)")
-    ap.add_argument("--dtype", default="int64", choices=sorted(BYTES))
+    ap.add_argument("--dtype", default=None, choices=sorted(BYTES),
+                    help="key type (default int64; batch workload: int32)")
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--pivot", default="exact", choices=["exact", "regular"])
     ap.add_argument("--n-blocks", type=int, default=0)
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "table1", "merge_ablation"])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the library's autotuner before timing (single and batch workloads)")
     ap.add_argument("--merge-variant", default="tree", choices=["tree", "sort", "select"],
                     help="step 4 chunk merge (single workload)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
@@ -60,6 +63,8 @@ def parse():
     a = ap.parse_args()
     if a.n is None and a.workload not in ("table1", "merge_ablation"):
         a.n = 1 << 30
+    if a.dtype is None:
+        a.dtype = "int32" if a.workload == "batch" else "int64"
     return a
 
 
@@ -218,6 +223,8 @@ def run_batch(a):
     keys = torch.empty_like(pristine)
     o_dev = torch.from_numpy(offs).to(dev)
     stream = torch.cuda.current_stream()
+    if not a.no_autotune:
+        ps.autotune(a.dtype, a.pivot, 1 << 14, 1 << 22, batched=True)  # untimed
     for _ in range(a.warmup):
         keys.copy_(pristine)
         ps.sort_batch(keys, o_dev, a.pivot)
@@ -261,6 +268,8 @@ def run_batch(a):
         "data": "synthetic (SplitMix64, seeded), resident in HBM",
         "config": {"workload": "batch of %d segments, lengths floor(2^U), U~U[6,22], %s %s, %s splitting"
                                % (a.segments, a.dtype, a.dist, a.pivot),
+                   "params": "size bins autotuned (ps_autotune batched, untimed)" if not a.no_autotune
+                   else "size heuristic",
                    "keys": n, "keys_per_s": n / (ms / 1e3)},
         "per_segment_ps_sort": {"segments": nb, "keys": base_keys, "ms": base_ms,
                                 "value": nb / (base_ms / 1e3), "unit": "segments/s",
@@ -638,6 +647,11 @@ def main():
     pristine = pristine.view(tdt)
     keys = torch.empty_like(pristine)
     stream = torch.cuda.current_stream()
+    tuned = False
+    if not a.no_autotune and not a.n_blocks and not a.n_parts and n >= (1 << 14):
+        # untimed: the library's autotuner picks n_B, n_P for this size
+        ps.autotune(a.dtype, a.pivot, n, n)
+        tuned = True
     nb, np_ = ps.resolve_params(n, {"int32": 0, "int64": 1, "float32": 2, "float64": 3,
                                     "uint32": 4, "uint64": 5}[a.dtype], a.n_blocks, a.n_parts)
 
@@ -723,7 +737,9 @@ def main():
                                        "float64": "f64", "uint32": "u32", "uint64": "u64"}[a.dtype],
         "data": "synthetic (SplitMix64, seeded), resident in HBM",
         "config": {"workload": wl, "n": n, "dist": a.dist, "pivot": a.pivot, "n_blocks": nb,
-                   "n_parts": np_, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "n_parts": np_, "params": "autotuned (ps_autotune, untimed)" if tuned else
+                   ("explicit" if a.n_blocks or a.n_parts else "size heuristic"),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (no flush needed)",
                    "restore": "keys restored from a pristine device copy before each step, outside the timed events",
                    "in_block_merge_passes": inblock_passes},

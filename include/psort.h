@@ -166,8 +166,30 @@ int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dt
 int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode,
                  const ps_params* params, ps_stream_t stream);
 
+/* Autotuner.  Times candidate (n_blocks, n_parts) pairs around the size
+ * heuristic (n_B in {d/2, d, 2d, 4d}, n_P in {n_B/2, n_B, 2 n_B}) on seeded
+ * uniform keys of `dtype`'s width for every power-of-two size 2^b in
+ * [max(n_min, 2^14), n_max], and records the fastest pair per (key width, b)
+ * in a process-wide table that automatic parameters then use for sorts of
+ * round(log2 n) = b.  batched = 0 tunes single sorts; batched = 1 tunes the
+ * size bins of ps_sort_batch (batches of about 2^26 keys in segments of
+ * (2^(b-1), 2^b] keys) and fills a separate table.  Keys per thread and
+ * threads per CTA are compile-time constants and are not tuned.  Allocates
+ * 2 * max(n_max, 2^26) keys of workspace; waits for `stream` (each candidate
+ * is timed with CUDA events: one untimed run, median of three).  n_max at
+ * most 2^34. */
+int ps_autotune(int dtype, int pivot_mode, int64_t n_min, int64_t n_max, int batched, ps_stream_t stream);
+
+/* Read (PS_ERR_NOT_FOUND when untuned) or write one entry of the tuned table:
+ * out/p->n_blocks and n_parts for sorts of round(log2 n) = log2_n keys of
+ * dtype's width.  ps_autotune_set with p NULL (or both fields 0) clears the
+ * entry; it lets a caller restore a table saved from an earlier run. */
+int ps_autotune_get(int dtype, int batched, int log2_n, ps_params* out);
+int ps_autotune_set(int dtype, int batched, int log2_n, const ps_params* p);
+
 /* The parameters a sort of n keys of `dtype` would use: copies `in` (or
- * zeros when NULL) to `out` with every automatic field resolved. */
+ * zeros when NULL) to `out` with every automatic field resolved (tuned
+ * entries first, then the size heuristic). */
 int ps_resolve_params(int64_t n, int dtype, const ps_params* in, ps_params* out);
 
 /* Bytes of workspace one sort of n keys of `dtype` takes from the pool

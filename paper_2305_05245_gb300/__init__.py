@@ -18,7 +18,8 @@ from ._lib import PS_PIVOT_EXACT, PS_PIVOT_REGULAR, PsortError  # noqa: F401
 
 __all__ = ["sort", "sort_pairs", "sort_host", "resolve_params", "workspace_bytes", "Trace",
            "PsortError", "PS_PIVOT_EXACT", "PS_PIVOT_REGULAR", "profile_enable", "profile_read",
-           "profile_reset", "sort_noalloc", "sort_batch", "sort_struct", "Server"]
+           "profile_reset", "sort_noalloc", "sort_batch", "sort_struct", "Server", "autotune",
+           "autotune_table", "autotune_set"]
 
 _MODES = {"regular": _lib.PS_PIVOT_REGULAR, "psrs": _lib.PS_PIVOT_REGULAR, 0: 0,
           "exact": _lib.PS_PIVOT_EXACT, "pses": _lib.PS_PIVOT_EXACT, 1: 1}
@@ -184,6 +185,48 @@ def sort_struct(records, record_bytes: int | None = None, key_offset: int = 0, p
     rc = lib.ps_sort_struct(records.data_ptr() if n else None, n, record_bytes, key_offset, _mode(pivot_mode),
                             ctypes.byref(_params(n_blocks, n_parts)), _stream_handle(stream))
     _lib.check(lib, "ps_sort_struct", rc)
+
+
+def _code_of(dtype) -> int:
+    import torch
+    if isinstance(dtype, int):
+        return dtype
+    if isinstance(dtype, str):
+        dtype = getattr(torch, dtype)
+    return _dtype_code(dtype)
+
+
+def autotune(dtype, pivot_mode="exact", n_min: int = 1 << 14, n_max: int = 1 << 26, batched: bool = False,
+             stream=None) -> dict:
+    """Run the library's autotuner (ps_autotune) for keys of ``dtype``'s width
+    over the power-of-two sizes in [n_min, n_max]; returns the tuned table
+    {log2 n: (n_blocks, n_parts)} that automatic parameters now use."""
+    lib = _lib.load()
+    code = _code_of(dtype)
+    rc = lib.ps_autotune(code, _mode(pivot_mode), n_min, n_max, 1 if batched else 0, _stream_handle(stream))
+    _lib.check(lib, "ps_autotune", rc)
+    return autotune_table(dtype, batched)
+
+
+def autotune_table(dtype, batched: bool = False) -> dict:
+    """The tuned entries {log2 n: (n_blocks, n_parts)} for ``dtype``'s width."""
+    lib = _lib.load()
+    code = _code_of(dtype)
+    out = {}
+    for b in range(64):
+        p = _lib.PsParams()
+        if lib.ps_autotune_get(code, 1 if batched else 0, b, ctypes.byref(p)) == 0:
+            out[b] = (p.n_blocks, p.n_parts)
+    return out
+
+
+def autotune_set(dtype, log2_n: int, n_blocks: int, n_parts: int, batched: bool = False) -> None:
+    """Write (or, with zeros, clear) one tuned entry, e.g. to restore a saved table."""
+    lib = _lib.load()
+    p = _lib.PsParams()
+    p.n_blocks, p.n_parts = n_blocks, n_parts
+    _lib.check(lib, "ps_autotune_set", lib.ps_autotune_set(_code_of(dtype), 1 if batched else 0, log2_n,
+                                                            ctypes.byref(p)))
 
 
 def sort_host(arr, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, stream=None) -> None:

@@ -22,7 +22,8 @@ PS_PIVOT_REGULAR, PS_PIVOT_EXACT = 0, 1
 EXPORTS = ["ps_sort", "ps_sort_ex", "ps_sort_pairs", "ps_sort_host", "ps_resolve_params",
            "ps_workspace_bytes", "ps_status_string", "ps_last_cuda_error", "ps_profile_enable",
            "ps_profile_read", "ps_profile_reset", "ps_sort_noalloc", "ps_debug_violation", "ps_sort_batch",
-           "ps_server_open", "ps_server_submit", "ps_server_poll", "ps_server_close", "ps_sort_struct"]
+           "ps_server_open", "ps_server_submit", "ps_server_poll", "ps_server_close", "ps_sort_struct",
+           "ps_autotune", "ps_autotune_get", "ps_autotune_set"]
 
 PS_NOALLOC_MAX_KEYS = 1 << 20
 PS_STRUCT_MAX_BYTES = 4096
@@ -84,6 +85,9 @@ def load(path: str | None = None):
     lib.ps_sort_noalloc.argtypes = [vp, i64, i32, i32, vp]
     lib.ps_sort_batch.argtypes = [vp, i64, vp, i32, i32, vp]
     lib.ps_sort_struct.argtypes = [vp, i64, i64, i64, i32, ctypes.POINTER(PsParams), vp]
+    lib.ps_autotune.argtypes = [i32, i32, i64, i64, i32, vp]
+    lib.ps_autotune_get.argtypes = [i32, i32, i32, ctypes.POINTER(PsParams)]
+    lib.ps_autotune_set.argtypes = [i32, i32, i32, ctypes.POINTER(PsParams)]
     lib.ps_server_open.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
     lib.ps_server_submit.argtypes = [vp, vp, i64, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
     lib.ps_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32), i32,
@@ -96,7 +100,8 @@ def load(path: str | None = None):
     for name in ("ps_sort", "ps_sort_ex", "ps_sort_pairs", "ps_sort_host", "ps_resolve_params",
                  "ps_workspace_bytes", "ps_last_cuda_error", "ps_profile_enable", "ps_profile_read",
                  "ps_profile_reset", "ps_sort_noalloc", "ps_debug_violation", "ps_sort_batch", "ps_server_open",
-                 "ps_server_submit", "ps_server_poll", "ps_server_close", "ps_sort_struct"):
+                 "ps_server_submit", "ps_server_poll", "ps_server_close", "ps_sort_struct", "ps_autotune",
+                 "ps_autotune_get", "ps_autotune_set"):
         getattr(lib, name).restype = i32
     if path is None:
         _lib = lib

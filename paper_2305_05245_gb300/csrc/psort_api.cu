@@ -132,7 +132,46 @@ static int64_t pow2_floor(int64_t x)
 // 2^28 keys, 128 at 2^30).  Exact splitting costs O(n_P * n_B * log^2 L)
 // probes (Sec. 2.3), so n_P stays <= min(n_B, 256); the final merge cuts
 // partitions into chunks on its own.
-static void resolve(int64_t n, int dtype, const ps_params* in, ps_params* out)
+//
+// Autotuned parameters (ps_autotune) take precedence over these defaults for
+// automatic fields: g_tune[context][family][round(log2 n)] holds (n_B, n_P)
+// measured fastest for sorts of about n keys, context 0 for single sorts and
+// 1 for the size bins of batched sorts; family 0 = 32-bit keys, 1 = 64-bit.
+struct TuneEntry {
+    int32_t nb, np;
+};
+static std::mutex g_tune_mu;
+static TuneEntry g_tune[2][2][64];
+
+static int tune_family(int dtype)
+{
+    if (dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32) return 0;
+    if (dtype == PS_I64 || dtype == PS_F64 || dtype == PS_U64) return 1;
+    return -1;
+}
+
+static int tune_bin(int64_t n)
+{
+    int b = 0;
+    while (b < 62 && (int64_t(1) << (b + 1)) <= n) b++;  // floor(log2 n)
+    // round to the nearer power of two
+    if (b < 62 && (double)n >= 1.41421356 * (double)(int64_t(1) << b)) b++;
+    return b;
+}
+
+static bool tuned(int ctx, int dtype, int64_t n, int32_t* nb, int32_t* np)
+{
+    const int f = tune_family(dtype);
+    if (f < 0 || n < 2) return false;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const TuneEntry& e = g_tune[ctx][f][tune_bin(n)];
+    if (e.nb <= 0) return false;
+    *nb = e.nb;
+    *np = e.np;
+    return true;
+}
+
+static void resolve_heuristic(int64_t n, int dtype, const ps_params* in, ps_params* out)
 {
     ps_params r;
     memset(&r, 0, sizeof(r));
@@ -144,6 +183,25 @@ static void resolve(int64_t n, int dtype, const ps_params* in, ps_params* out)
     if (r.n_blocks <= 0) r.n_blocks = nb;
     if (r.n_parts <= 0) r.n_parts = std::min<int64_t>(256, std::max<int64_t>(1, r.n_blocks));
     *out = r;
+}
+
+void resolve_default(int64_t n, int dtype, ps_params* out) { resolve_heuristic(n, dtype, nullptr, out); }
+
+// Automatic fields: a tuned entry for this size (context ctx) when there is
+// one, else the heuristic.  Explicit fields are kept.
+static void resolve(int64_t n, int dtype, const ps_params* in, ps_params* out, int ctx = 0)
+{
+    ps_params r;
+    memset(&r, 0, sizeof(r));
+    if (in) r = *in;
+    int32_t nb = 0, np = 0;
+    if ((r.n_blocks <= 0 || r.n_parts <= 0) && tuned(ctx, dtype, n, &nb, &np)) {
+        if (r.n_blocks <= 0) {
+            r.n_blocks = nb;
+            if (r.n_parts <= 0) r.n_parts = np;
+        }
+    }
+    resolve_heuristic(n, dtype, &r, out);
 }
 
 static int check_params(const ps_params* p)
@@ -218,7 +276,7 @@ size_t sort_ws_bytes(int64_t n, int dtype)
 // Batched sort of the segments [off[i], off[i+1]) of `keys` (host offsets):
 // bins by length, one multi-instance pipeline per bin, queued on s.
 int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
-               int64_t* pinned, size_t pinned_cap)
+               int64_t* pinned, size_t pinned_cap, const ps_params* force)
 {
     const int64_t n_segs = (int64_t)off.size() - 1;
     if (n_segs <= 0) return PS_OK;
@@ -284,8 +342,10 @@ int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode,
         memset(&r, 0, sizeof(r));
         if (b == 0) {
             r.n_blocks = r.n_parts = 1;  // one tile: the block sort is the whole sort
+        } else if (force) {
+            r = *force;
         } else {
-            resolve(nmax, dtype, nullptr, &r);
+            resolve(nmax, dtype, nullptr, &r, 1);
         }
         SortArgs a;
         a.keys = keys;
@@ -306,6 +366,139 @@ int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode,
         rc = dispatch(a);
     }
     ws_free(dev, s);
+    return rc;
+}
+
+// ------------------------------------------------------------- autotuner
+// Uniform 64-bit words from SplitMix64 (Steele, Lea & Flood 2014) for the
+// tuning inputs: word i of stream s is mix(s + (i + 1) * golden gamma).
+__global__ void k_tune_fill(uint64_t* w, int64_t nwords, uint64_t seed)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        w[i] = z ^ (z >> 31);
+    }
+}
+
+// Median of `reps` timed runs of f() on stream s (after one untimed run);
+// restore() runs before each, outside the timed events.
+template <typename F, typename R>
+static int time_median(F f, R restore, cudaStream_t s, int reps, float* ms)
+{
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return fail_cuda(e);
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail_cuda(e);
+    }
+    std::vector<float> t;
+    int rc = PS_OK;
+    for (int i = 0; i <= reps && rc == PS_OK; i++) {
+        if ((rc = restore()) != PS_OK) break;
+        if ((e = cudaEventRecord(e0, s)) != cudaSuccess) { rc = fail_cuda(e); break; }
+        if ((rc = f()) != PS_OK) break;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess) { rc = fail_cuda(e); break; }
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = fail_cuda(e); break; }
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        if (i > 0) t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PS_OK) return rc;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return PS_OK;
+}
+
+// Candidates around the heuristic d: n_B in {d/2, d, 2d, 4d}, n_P in
+// {n_B/2, n_B, 2 n_B} (within the limits).
+static std::vector<std::pair<int64_t, int64_t>> tune_candidates(int64_t n, int dtype)
+{
+    ps_params d;
+    resolve_heuristic(n, dtype, nullptr, &d);
+    std::vector<std::pair<int64_t, int64_t>> c;
+    for (int64_t nb : {d.n_blocks / 2, d.n_blocks, d.n_blocks * 2, d.n_blocks * 4}) {
+        if (nb < 1 || nb > MAX_BLOCKS) continue;
+        for (int64_t np : {nb / 2, nb, nb * 2}) {
+            if (np < 1 || np > 1024) continue;
+            bool dup = false;
+            for (auto& x : c) dup = dup || (x.first == nb && x.second == np);
+            if (!dup) c.push_back({nb, np});
+        }
+    }
+    return c;
+}
+
+static int autotune(int dtype, int mode, int64_t n_min, int64_t n_max, int batched, cudaStream_t s)
+{
+    const int f = tune_family(dtype);
+    const size_t kb = f == 0 ? 4 : 8;
+    int b0 = 14;
+    while ((int64_t(1) << b0) < n_min) b0++;
+    int b1 = b0;
+    while (b1 < 62 && (int64_t(1) << (b1 + 1)) <= n_max) b1++;
+    if ((int64_t(1) << b1) > n_max) return PS_OK;  // no power of two in range
+    // batched bins: segments of about 2^b keys, 2^26 keys per batch (at least 2 segments)
+    const int64_t nkeys = batched ? std::max<int64_t>(int64_t(1) << 26, int64_t(2) << b1) : int64_t(1) << b1;
+    char* buf = nullptr;
+    int rc = ws_alloc((void**)&buf, 2 * (size_t)nkeys * kb + 512, s);
+    if (rc != PS_OK) return rc;
+    char* keys = buf;
+    char* pristine = buf + (((size_t)nkeys * kb + 255) & ~(size_t)255);
+    k_tune_fill<<<1024, 256, 0, s>>>((uint64_t*)pristine, (int64_t)(nkeys * kb / 8), 0x5EED5EED5EEDull);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = fail_cuda(e);
+    for (int b = b0; b <= b1 && rc == PS_OK; b++) {
+        const int64_t n = int64_t(1) << b;
+        std::vector<int64_t> off;
+        int64_t used = n;
+        if (batched) {
+            // lengths spread over (2^(b-1), 2^b], the batch bin of 2^b
+            off.push_back(0);
+            int64_t i = 0;
+            while (off.back() + n <= nkeys) {
+                const int64_t len = n / 2 + 1 + (int64_t)(((uint64_t)(i * 0x9E3779B97F4A7C15ull) >> 40) % (uint64_t)(n / 2));
+                off.push_back(off.back() + len);
+                i++;
+            }
+            used = off.back();
+        }
+        auto restore = [&]() {
+            cudaError_t ce = cudaMemcpyAsync(keys, pristine, (size_t)used * kb, cudaMemcpyDeviceToDevice, s);
+            return ce == cudaSuccess ? PS_OK : fail_cuda(ce);
+        };
+        float best = 1e30f;
+        int64_t bnb = 0, bnp = 0;
+        for (auto& cand : tune_candidates(n, dtype)) {
+            ps_params p;
+            memset(&p, 0, sizeof(p));
+            p.n_blocks = cand.first;
+            p.n_parts = cand.second;
+            auto run = [&]() {
+                if (batched) return batch_sort(off, keys, dtype, mode, s, nullptr, 0, &p);
+                return sort_common(keys, nullptr, n, dtype, mode, &p, nullptr, s);
+            };
+            float ms = 0.f;
+            rc = time_median(run, restore, s, 3, &ms);
+            if (rc != PS_OK) break;
+            if (ms < best) {
+                best = ms;
+                bnb = cand.first;
+                bnp = cand.second;
+            }
+        }
+        if (rc == PS_OK && bnb > 0) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[batched ? 1 : 0][f][b] = TuneEntry{(int32_t)bnb, (int32_t)bnp};
+        }
+    }
+    ws_free(buf, s);
     return rc;
 }
 
@@ -418,6 +611,45 @@ int ps_workspace_bytes(int64_t n, int dtype, const ps_params* params, size_t* ou
     case -1: *out = ws_bytes_rec(n, r.n_blocks, r.n_parts); break;
     default: *out = ws_bytes_u64(n, r.n_blocks, r.n_parts); break;
     }
+    return PS_OK;
+}
+
+int ps_autotune(int dtype, int pivot_mode, int64_t n_min, int64_t n_max, int batched, ps_stream_t stream)
+{
+    if (tune_family(dtype) < 0) return PS_ERR_UNSUPPORTED;
+    if (pivot_mode != PS_PIVOT_REGULAR && pivot_mode != PS_PIVOT_EXACT) return PS_ERR_UNSUPPORTED;
+    if (n_min < 2 || n_max < n_min || n_max > (int64_t(1) << 34)) return PS_ERR_INVALID_ARG;
+    if (batched != 0 && batched != 1) return PS_ERR_INVALID_ARG;
+    return autotune(dtype, pivot_mode, n_min, n_max, batched, (cudaStream_t)stream);
+}
+
+int ps_autotune_get(int dtype, int batched, int log2_n, ps_params* out)
+{
+    const int f = tune_family(dtype);
+    if (f < 0) return PS_ERR_UNSUPPORTED;
+    if (!out || log2_n < 0 || log2_n > 63 || (batched != 0 && batched != 1)) return PS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const TuneEntry& e = g_tune[batched][f][log2_n];
+    if (e.nb <= 0) return PS_ERR_NOT_FOUND;
+    memset(out, 0, sizeof(*out));
+    out->n_blocks = e.nb;
+    out->n_parts = e.np;
+    return PS_OK;
+}
+
+int ps_autotune_set(int dtype, int batched, int log2_n, const ps_params* p)
+{
+    const int f = tune_family(dtype);
+    if (f < 0) return PS_ERR_UNSUPPORTED;
+    if (log2_n < 0 || log2_n > 63 || (batched != 0 && batched != 1)) return PS_ERR_INVALID_ARG;
+    TuneEntry t{0, 0};
+    if (p && (p->n_blocks != 0 || p->n_parts != 0)) {
+        if (p->n_blocks < 1 || p->n_blocks > MAX_BLOCKS || p->n_parts < 1 || p->n_parts > MAX_PARTS)
+            return PS_ERR_INVALID_ARG;
+        t = TuneEntry{(int32_t)p->n_blocks, (int32_t)p->n_parts};
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[batched][f][log2_n] = t;
     return PS_OK;
 }
 

@@ -68,8 +68,11 @@ int viol_read_rec(unsigned long long* out);
 // Batched sort of the segments [off[i], off[i+1]) of keys (host offsets).
 // pinned (optional): page-locked host scratch of pinned_cap int64 for the
 // instance table; when given, the call does not wait for the stream.
+// force (optional): n_B/n_P for every bin above the one-tile bin (tuning).
 int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
-               int64_t* pinned, size_t pinned_cap);
+               int64_t* pinned, size_t pinned_cap, const ps_params* force = nullptr);
+// The size heuristic alone (no tuned entries), with every field automatic.
+void resolve_default(int64_t n, int dtype, ps_params* out);
 // Records (uint64 key, uint32 payload) through the validated record path.
 int sort_records(uint64_t* keys, uint32_t* payload, int64_t n, int mode, const ps_params* params, cudaStream_t s);
 // Fixed-size records sorted by an embedded uint64 key (arguments validated).

@@ -46,11 +46,11 @@ extern "C" int ps_sort_noalloc(void* keys, int64_t n, int dtype, int pivot_mode,
     if (n <= 1) return PS_OK;
     const bool narrow = dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32;
     if (!keys || (uintptr_t)keys % (narrow ? 4 : 8) != 0) return PS_ERR_INVALID_ARG;
+    // the size heuristic, not tuned entries: the scratch is sized for it
     ps_params r;
-    int rc = ps_resolve_params(n, dtype, nullptr, &r);
-    if (rc != PS_OK) return rc;
+    resolve_default(n, dtype, &r);
     void* ws = nullptr;
-    rc = noalloc_scratch(&ws);
+    int rc = noalloc_scratch(&ws);
     if (rc != PS_OK) return rc;
     SortArgs a;
     a.keys = keys;

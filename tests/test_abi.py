@@ -80,6 +80,36 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ps_sort_host(None, 5, 0, 0, None, None) == -1
 
 
+def test_autotune_table_without_gpu(lib):
+    """ps_autotune's argument checks and the tuned table's get/set (no GPU)."""
+    from paper_2305_05245_gb300 import _lib
+    p = _lib.PsParams()
+    assert lib.ps_autotune(-1, 1, 1 << 14, 1 << 16, 0, None) == -2
+    assert lib.ps_autotune(0, 9, 1 << 14, 1 << 16, 0, None) == -2
+    assert lib.ps_autotune(0, 1, 1, 1 << 16, 0, None) == -1
+    assert lib.ps_autotune(0, 1, 1 << 16, 1 << 14, 0, None) == -1
+    assert lib.ps_autotune(0, 1, 1 << 14, 1 << 16, 2, None) == -1
+    assert lib.ps_autotune_get(0, 0, 40, ctypes.byref(p)) == -7
+    assert lib.ps_autotune_get(9, 0, 40, ctypes.byref(p)) == -2
+    p.n_blocks, p.n_parts = 5000, 4
+    assert lib.ps_autotune_set(0, 0, 40, ctypes.byref(p)) == -1
+    p.n_blocks, p.n_parts = 48, 96
+    assert lib.ps_autotune_set(2, 0, 40, ctypes.byref(p)) == 0   # float32 shares the 32-bit entry
+    q = _lib.PsParams()
+    assert lib.ps_autotune_get(4, 0, 40, ctypes.byref(q)) == 0 and (q.n_blocks, q.n_parts) == (48, 96)
+    assert lib.ps_autotune_get(1, 0, 40, ctypes.byref(q)) == -7  # 64-bit keys: separate entry
+    assert lib.ps_autotune_get(0, 1, 40, ctypes.byref(q)) == -7  # batched table: separate
+    r = _lib.PsParams()
+    assert lib.ps_resolve_params(1 << 40, 0, None, ctypes.byref(r)) == 0
+    assert (r.n_blocks, r.n_parts) == (48, 96)
+    r2 = _lib.PsParams()
+    r2.n_blocks = 64
+    assert lib.ps_resolve_params(1 << 40, 0, ctypes.byref(r2), ctypes.byref(r)) == 0
+    assert r.n_blocks == 64  # explicit fields win
+    assert lib.ps_autotune_set(0, 0, 40, None) == 0
+    assert lib.ps_autotune_get(0, 0, 40, ctypes.byref(q)) == -7
+
+
 def test_resolve_and_workspace(lib):
     import paper_2305_05245_gb300 as ps
     nb, np_ = ps.resolve_params(1 << 26, 0)
