@@ -367,15 +367,9 @@ __device__ __forceinline__ void serial_merge(const S& s, int ai, int aend, int b
         if (!STOP || i < cnt) {
             const bool p = (bi >= bend) || ((ai < aend) && !S::lt(b, a));
             out[i] = p ? a : b;
-            const int nx = p ? ai + 1 : bi + 1;
-            const V c = s.ld(nx);
-            if (p) {
-                a = c;
-                ai = nx;
-            } else {
-                b = c;
-                bi = nx;
-            }
+            // advance the side that was taken (predicated loads, no selects)
+            if (p) a = s.ld(++ai);
+            else b = s.ld(++bi);
         }
     }
 }
