@@ -758,9 +758,14 @@ template <typename K> struct Splitter {
 // lists, stable, so ties order by run then position).  Splitter j (1..J-1) is
 // the first sample whose cumulative weight reaches j*M/J; child j-1 ends with
 // it (inclusive) and child j starts after it.
+// The sorted pool also bounds every co-rank: if c samples of run r precede
+// splitter j in the pool, the splitter's co-rank in run r lies in
+// [c*S, min(c*S + S - 1, len_r)] (all samples: exactly len_r).  These windows
+// go to the child level's lo/hi tables, where k_corank narrows them to the
+// exact co-rank with a search over at most S elements.
 template <int NT, int E, typename K>
 __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t* choff, int* chgrp,
-                                             Splitter<K>* spl, int64_t ccap)
+                                             Splitter<K>* spl, int64_t ccap, Level C)
 {
     constexpr int POOL = NT * E;
     extern __shared__ __align__(16) char smem[];
@@ -773,18 +778,28 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
     // every slot first holds a splitter above all keys, so that a slot the
     // assignment below could miss yields an empty child (and an oversized
     // sibling, merged exactly) rather than stale bytes
+    const int Kr = L.K;
+    const int64_t* lo = L.lo + g * Kr;
+    const int64_t* hi = L.hi + g * Kr;
     for (int64_t j = threadIdx.x; j < J; j += NT) {
         chgrp[c0 + j] = (int)g;
         spl[c0 + j] = Splitter<K>{KT<K>::maxkey(), 0xFFFFFFFFu, 0xFFFFFFFFu};
     }
+    // default co-rank windows: the whole run
+    for (int64_t t = threadIdx.x; t < (J - 1) * Kr; t += NT) {
+        const int64_t c = c0 + 1 + t / Kr;
+        const int r = (int)(t % Kr);
+        if (!PS_IN(c, C.cap, 35)) continue;
+        C.lo[c * Kr + r] = lo[r];
+        C.hi[c * Kr + r] = hi[r] > lo[r] ? hi[r] : lo[r];
+    }
     if (J <= 1) return;
     __syncthreads();
-    const int Kr = L.K;
-    const int64_t* lo = L.lo + g * Kr;
-    const int64_t* hi = L.hi + g * Kr;
     char* sp = smem;
     STagged<K> pool{SBuf<K>::carve(sp, POOL), SBuf<uint64_t>::carve(sp, POOL)};
-    int* off = (int*)sp;
+    int* mpos = (int*)sp;                 // pool position of every run's i-th sample
+    int* jpos = mpos + POOL;              // pool position of splitter j (-1: none)
+    int* off = jpos + (POOL / 2 + 1);
     const int64_t M = L.size[g];
     // about max(2K, 96) samples per child: enough to place every splitter
     // within a few percent of its target rank (each run's co-rank is known
@@ -804,6 +819,7 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
         ex += (hi[r] - lo[r] + S - 1) / S;
     }
     if (threadIdx.x == 0) off[Kr] = (int)P64;
+    for (int64_t j = threadIdx.x; j < J && j <= POOL / 2; j += NT) jpos[j] = -1;
     __syncthreads();
     const int P = (int)P64;  // <= M/S + K <= POOL
     if (!PS_IN(P, POOL + 1, 23) || P > POOL) return;
@@ -835,6 +851,8 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
             if (!PS_IN(x, Kr, 25)) continue;
             const int64_t q = (int64_t)(uint32_t)tag, len = hi[x] - lo[x];
             wsum += (q == len - 1 && len % S) ? len % S : S;
+            const int64_t slot = off[x] + q / S;  // the sample's ordinal within its run
+            if (PS_IN(slot, off[x + 1], 36) && slot < off[x + 1]) mpos[slot] = q0 + i;
         }
     }
     int64_t tot;
@@ -862,10 +880,36 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
                 int64_t t = muldiv(j, M, J) - adj;
                 if (t < 1) t = 1;
                 if (t > ci) break;
-                if (t > cb) spl[c0 + j] = Splitter<K>{e.key, (uint32_t)x, (uint32_t)q};
+                if (t > cb) {
+                    spl[c0 + j] = Splitter<K>{e.key, (uint32_t)x, (uint32_t)q};
+                    if (j <= POOL / 2) jpos[j] = q0 + i;
+                }
             }
             cb = ci;
         }
+    }
+    __syncthreads();
+    // co-rank windows of splitters 1..J-1 in every run: c = run r's samples
+    // ahead of the splitter in the pool (binary search of their positions)
+    for (int64_t t = threadIdx.x; t < (J - 1) * Kr; t += NT) {
+        const int64_t j = 1 + t / Kr;
+        const int r = (int)(t % Kr);
+        const int m = j <= POOL / 2 ? jpos[j] : -1;
+        if (m < 0) continue;  // unassigned: the whole run (maximal key)
+        int a = off[r], b = off[r + 1];
+        const int base = a;
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (mpos[mid] < m) a = mid + 1;
+            else b = mid;
+        }
+        const int64_t c = a - base, len = hi[r] - lo[r];
+        const int64_t wlo = c * S < len ? c * S : len;
+        const int64_t whi = c * S + S - 1 < len ? c * S + S - 1 : len;
+        const int64_t cc = c0 + j;
+        if (!PS_IN(cc, C.cap, 37)) continue;
+        C.lo[cc * Kr + r] = lo[r] + wlo;
+        C.hi[cc * Kr + r] = lo[r] + whi;
     }
 }
 
@@ -892,8 +936,12 @@ __global__ void k_corank(Level L, GBuf<K> src, const Splitter<K>* spl, const int
         v = lo;
     } else {
         const Splitter<K> e = spl[c];
-        if ((uint32_t)r < e.run) v = lo + bound<false>(src, lo, hi, e.key);
-        else if ((uint32_t)r > e.run) v = lo + bound<true>(src, lo, hi, e.key);
+        // the sample pool's window for this co-rank (within the run)
+        int64_t a = C.lo[c * Kr + r], b = C.hi[c * Kr + r];
+        a = a < lo ? lo : (a > hi ? hi : a);
+        b = b < a ? a : (b > hi ? hi : b);
+        if ((uint32_t)r < e.run) v = a + bound<false>(src, a, b, e.key);
+        else if ((uint32_t)r > e.run) v = a + bound<true>(src, a, b, e.key);
         else v = lo + (int64_t)e.pos + 1;
         v = v < lo ? lo : (v > hi ? hi : v);
     }

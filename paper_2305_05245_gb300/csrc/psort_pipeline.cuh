@@ -15,10 +15,10 @@ namespace ps {
 // (PNT, PE; PNT*PE samples).
 template <typename K> struct Cfg;
 template <> struct Cfg<uint32_t> {
-    static constexpr int TNT = 512, TE = 16, MNT = 1024, ME = 16, PNT = 512, PE = 16;
+    static constexpr int TNT = 512, TE = 16, MNT = 1024, ME = 16, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<uint64_t> {
-    static constexpr int TNT = 512, TE = 16, MNT = 512, ME = 16, PNT = 512, PE = 16;
+    static constexpr int TNT = 512, TE = 16, MNT = 512, ME = 16, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<Rec> {
     static constexpr int TNT = 512, TE = 8, MNT = 1024, ME = 8, PNT = 512, PE = 8;
@@ -229,7 +229,10 @@ template <typename K> struct Pipeline {
     static constexpr int TNT = C::TNT, TE = C::TE, MNT = C::MNT, ME = C::ME, PNT = C::PNT, PE = C::PE;
     static constexpr int T = TNT * TE, CAP = MNT * ME, POOL = PNT * PE;
 
-    static size_t pool_smem(int Kr) { return STagged<K>::bytes(POOL) + 4 * (size_t)(Kr + 1) + 64; }
+    static size_t pool_smem(int Kr)
+    {
+        return STagged<K>::bytes(POOL) + 4 * (size_t)POOL + 4 * (size_t)(POOL / 2 + 1) + 4 * (size_t)(Kr + 1) + 64;
+    }
     static constexpr int BE = ME / 2;  // keys per thread of the oversized-group path
     static size_t merge_smem(int Kr) { return SBuf<K>::bytes(CAP) + 16 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
     static size_t big_smem(int Kr) { return SBuf<K>::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
@@ -298,7 +301,8 @@ template <typename K> struct Pipeline {
             }
             {
                 ProfScope ps_(fin ? "pool_final" : "pool_inblock", s);
-                fp<<<(unsigned)sh.G[l], PNT, pool_smem(Kr), s>>>(Lv[l], src, choff, chgrp, spl, sh.G[l + 1]);
+                fp<<<(unsigned)sh.G[l], PNT, pool_smem(Kr), s>>>(Lv[l], src, choff, chgrp, spl, sh.G[l + 1],
+                                                                 Lv[l + 1]);
             }
             {
                 ProfScope ps_(fin ? "corank_final" : "corank_inblock", s);
