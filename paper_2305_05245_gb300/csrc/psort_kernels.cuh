@@ -153,45 +153,61 @@ template <> struct GBuf<Rec> {
 template <int XF> __device__ __forceinline__ Rec xform(const Rec& x) { return x; }
 
 // ---------------------------------------------- shared-memory buffers (padded)
-// One pad slot after every 128 bytes, so that thread t reading its E
-// consecutive elements (blocked layout) hits distinct banks.
-template <typename K> struct SBuf;
-template <> struct SBuf<uint32_t> {
+// One pad slot after every W elements, so that thread t reading or writing
+// its E consecutive elements (blocked layout) hits distinct banks: W = 32 for
+// 4-byte keys; for 8-byte keys W = 16 when E <= 16 and W = 32 when E = 32
+// (a thread's 32 keys then span two 128-byte rows; with W = 16 threads t and
+// t + 8 of a half-warp would share a bank).
+template <typename K> struct PadOf;
+template <> struct PadOf<uint32_t> { static constexpr int v = 32; };
+template <> struct PadOf<uint64_t> { static constexpr int v = 16; };
+template <> struct PadOf<Rec> { static constexpr int v = 16; };
+template <typename K, int E> struct TilePad {
+    static constexpr int v = (sizeof(K) == 8 && E >= 32) ? 32 : PadOf<K>::v;
+};
+
+template <typename K, int W = PadOf<K>::v> struct SBuf;
+constexpr int log2c(int w) { return w <= 1 ? 0 : 1 + log2c(w / 2); }
+template <int W> struct SBuf<uint32_t, W> {
+    static_assert((W & (W - 1)) == 0, "the pad period is a power of two");
     uint32_t* a;
     int cap;  // physical slots (checked builds only)
-    __device__ __forceinline__ uint32_t ld(int i) const { return PS_IN(i + (i >> 5), cap, 4) ? a[i + (i >> 5)] : 0u; }
-    __device__ __forceinline__ void st(int i, uint32_t v) const { if (PS_IN(i + (i >> 5), cap, 5)) a[i + (i >> 5)] = v; }
-    static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / 32 + 1) * 4 + 15) & ~(size_t)15; }
+    __device__ __forceinline__ static int at(int i) { return i + (i >> log2c(W)); }
+    __device__ __forceinline__ uint32_t ld(int i) const { return PS_IN(at(i), cap, 4) ? a[at(i)] : 0u; }
+    __device__ __forceinline__ void st(int i, uint32_t v) const { if (PS_IN(at(i), cap, 5)) a[at(i)] = v; }
+    static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / W + 1) * 4 + 15) & ~(size_t)15; }
     static __device__ SBuf carve(char*& sp, int n)
     {
-        SBuf b{(uint32_t*)sp, n + n / 32 + 1};
+        SBuf b{(uint32_t*)sp, n + n / W + 1};
         sp += bytes(n);
         return b;
     }
 };
-template <> struct SBuf<uint64_t> {
+template <int W> struct SBuf<uint64_t, W> {
+    static_assert((W & (W - 1)) == 0, "the pad period is a power of two");
     uint64_t* a;
     int cap;
-    __device__ __forceinline__ uint64_t ld(int i) const { return PS_IN(i + (i >> 4), cap, 4) ? a[i + (i >> 4)] : 0ull; }
-    __device__ __forceinline__ void st(int i, uint64_t v) const { if (PS_IN(i + (i >> 4), cap, 5)) a[i + (i >> 4)] = v; }
-    static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / 16 + 1) * 8 + 15) & ~(size_t)15; }
+    __device__ __forceinline__ static int at(int i) { return i + (i >> log2c(W)); }
+    __device__ __forceinline__ uint64_t ld(int i) const { return PS_IN(at(i), cap, 4) ? a[at(i)] : 0ull; }
+    __device__ __forceinline__ void st(int i, uint64_t v) const { if (PS_IN(at(i), cap, 5)) a[at(i)] = v; }
+    static __host__ __device__ size_t bytes(int n) { return (((size_t)n + n / W + 1) * 8 + 15) & ~(size_t)15; }
     static __device__ SBuf carve(char*& sp, int n)
     {
-        SBuf b{(uint64_t*)sp, n + n / 16 + 1};
+        SBuf b{(uint64_t*)sp, n + n / W + 1};
         sp += bytes(n);
         return b;
     }
 };
-template <> struct SBuf<Rec> {
-    SBuf<uint64_t> k;
+template <int W> struct SBuf<Rec, W> {
+    SBuf<uint64_t, W> k;
     SBuf<uint32_t> p;
     __device__ __forceinline__ Rec ld(int i) const { return Rec{k.ld(i), p.ld(i)}; }
     __device__ __forceinline__ void st(int i, const Rec& v) const { k.st(i, v.k); p.st(i, v.p); }
-    static __host__ __device__ size_t bytes(int n) { return SBuf<uint64_t>::bytes(n) + SBuf<uint32_t>::bytes(n); }
+    static __host__ __device__ size_t bytes(int n) { return SBuf<uint64_t, W>::bytes(n) + SBuf<uint32_t>::bytes(n); }
     static __device__ SBuf carve(char*& sp, int n)
     {
         SBuf b;
-        b.k = SBuf<uint64_t>::carve(sp, n);
+        b.k = SBuf<uint64_t, W>::carve(sp, n);
         b.p = SBuf<uint32_t>::carve(sp, n);
         return b;
     }
@@ -214,28 +230,31 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
-__device__ __forceinline__ void cp_elem(const SBuf<uint32_t>& s, int i, const GBuf<uint32_t>& g, int64_t j)
+template <int W>
+__device__ __forceinline__ void cp_elem(const SBuf<uint32_t, W>& s, int i, const GBuf<uint32_t>& g, int64_t j)
 {
-    if (PS_IN(i + (i >> 5), s.cap, 6) && PS_IN(j, g.n, 3)) cp_async4(s.a + i + (i >> 5), g.p + j);
+    if (PS_IN(s.at(i), s.cap, 6) && PS_IN(j, g.n, 3)) cp_async4(s.a + s.at(i), g.p + j);
 }
-__device__ __forceinline__ void cp_elem(const SBuf<uint64_t>& s, int i, const GBuf<uint64_t>& g, int64_t j)
+template <int W>
+__device__ __forceinline__ void cp_elem(const SBuf<uint64_t, W>& s, int i, const GBuf<uint64_t>& g, int64_t j)
 {
-    if (PS_IN(i + (i >> 4), s.cap, 6) && PS_IN(j, g.n, 3)) cp_async8(s.a + i + (i >> 4), g.p + j);
+    if (PS_IN(s.at(i), s.cap, 6) && PS_IN(j, g.n, 3)) cp_async8(s.a + s.at(i), g.p + j);
 }
-__device__ __forceinline__ void cp_elem(const SBuf<Rec>& s, int i, const GBuf<Rec>& g, int64_t j)
+template <int W>
+__device__ __forceinline__ void cp_elem(const SBuf<Rec, W>& s, int i, const GBuf<Rec>& g, int64_t j)
 {
-    if (PS_IN(i + (i >> 4), s.k.cap, 6) && PS_IN(j, g.n, 3)) {
-        cp_async8(s.k.a + i + (i >> 4), g.k + j);
-        cp_async4(s.p.a + i + (i >> 5), g.p + j);
+    if (PS_IN(s.k.at(i), s.k.cap, 6) && PS_IN(j, g.n, 3)) {
+        cp_async8(s.k.a + s.k.at(i), g.k + j);
+        cp_async4(s.p.a + s.p.at(i), g.p + j);
     }
 }
 
 // Storage views used by the merge routine: plain keys, or keys carrying a
 // 64-bit tag (run index and position of a pool sample).  Comparison is on
 // the key only; the merge is stable, so ties keep piece order.
-template <typename K> struct SKeys {
+template <typename K, int W = PadOf<K>::v> struct SKeys {
     using V = K;
-    SBuf<K> b;
+    SBuf<K, W> b;
     __device__ __forceinline__ V ld(int i) const { return b.ld(i); }
     __device__ __forceinline__ void st(int i, const V& v) const { b.st(i, v); }
     __device__ __forceinline__ static bool lt(const V& x, const V& y) { return key_lt(x, y); }
@@ -574,9 +593,10 @@ template <int NT, int E, typename K, int XF, bool FINAL>
 __global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst in, int64_t n_B, int64_t R0)
 {
     constexpr int T = NT * E;
+    constexpr int W = TilePad<K, E>::v;
     extern __shared__ __align__(16) char smem[];
     char* sp = smem;
-    SBuf<K> sb = SBuf<K>::carve(sp, T);
+    SBuf<K, W> sb = SBuf<K, W>::carve(sp, T);
     const int64_t per_inst = n_B * R0;
     const int64_t inst = blockIdx.x / per_inst;
     const int64_t rest = blockIdx.x - inst * per_inst;
@@ -601,7 +621,7 @@ __global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst
 #pragma unroll
     for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
     __syncthreads();
-    merge_levels_pow2<NT, E>(SKeys<K>{sb});
+    merge_levels_pow2<NT, E>(SKeys<K, W>{sb});
     for (int i = threadIdx.x; i < n; i += NT) {
         if (FINAL) dst.template stx<XF>(o + i, sb.ld(i));
         else dst.st(o + i, sb.ld(i));

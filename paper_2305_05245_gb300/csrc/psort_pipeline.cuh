@@ -236,7 +236,7 @@ template <typename K> struct Pipeline {
     static constexpr int BE = ME / 2;  // keys per thread of the oversized-group path
     static size_t merge_smem(int Kr) { return SBuf<K>::bytes(CAP) + 16 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
     static size_t big_smem(int Kr) { return SBuf<K>::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
-    static size_t tile_smem() { return SBuf<K>::bytes(T) + 64; }
+    static size_t tile_smem() { return SBuf<K, TilePad<K, TE>::v>::bytes(T) + 64; }
 
     static Inst inst_of(const Plan<K>& pl, const SortArgs& a)
     {
