@@ -1008,12 +1008,15 @@ __global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* chof
 // search window shrinks with the value interval: elements left of it are
 // known to be <= every remaining candidate, elements right of it are known
 // to be larger.  Runs are handled by threads in contiguous ranges of at most
-// MAXPER; all threads get the result.
-template <int NT, typename K, int MAXPER = 8>
+// MAXPER (enough for the largest n_B, 4096 runs, at NT threads); all threads
+// get the result.
+constexpr int MAX_RUNS = 4096;
+template <int NT, typename K, int MAXPER = (MAX_RUNS + NT - 1) / NT>
 __device__ K select_value(const GBuf<K>& src, const int64_t* a, const int64_t* b, int nruns, int64_t t)
 {
     using U = typename KT<K>::U;
     U lo = 0, hi = KT<K>::umax();
+    PS_IN(nruns, NT * MAXPER + 1, 38);  // more runs than the register windows hold
     const int per = (nruns + NT - 1) / NT;
     const int r0 = threadIdx.x * per;
     int64_t wa[MAXPER], wb[MAXPER];
@@ -1103,16 +1106,17 @@ __device__ void exact_corank(const GBuf<K>& src, const int64_t* a, const int64_t
 // is sorted as a whole, ignoring that the pieces are sorted (the "copy and
 // sort" way of multiway merging, Sec. 2.2).
 template <int NT, int E, typename K, int XF, bool BIG, bool ALIGNED, bool SORTCHUNK = false>
-__global__ void __launch_bounds__(NT, (!BIG && NT <= 512) ? 2 : 1) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
+__global__ void __launch_bounds__(NT, (!BIG && NT <= 256) ? 3 : (!BIG && NT <= 512) ? 2 : 1) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
                                               unsigned long long* nbig)
 {
     static_assert(!(BIG && ALIGNED), "the oversized-group path merges unpadded pieces");
     static_assert(!(SORTCHUNK && (BIG || ALIGNED)), "copy-and-sort chunks are unpadded and fit the capacity");
     constexpr int CAP = NT * E;
+    constexpr int W = TilePad<K, E>::v;
     extern __shared__ __align__(16) char smem[];
     const int Kr = C.K;
     char* sp = smem;
-    SBuf<K> sb = SBuf<K>::carve(sp, CAP);
+    SBuf<K, W> sb = SBuf<K, W>::carve(sp, CAP);
     int64_t* a = (int64_t*)sp;                       // window starts
     int64_t* b = BIG ? a + Kr : nullptr;             // window ends (BIG only)
     int64_t* x = BIG ? a + 2 * Kr : nullptr;         // sub-chunk ends (BIG only)
@@ -1192,11 +1196,11 @@ __global__ void __launch_bounds__(NT, (!BIG && NT <= 512) ? 2 : 1) k_merge(Level
 #pragma unroll
                 for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
                 __syncthreads();
-                merge_levels_pow2<NT, E>(SKeys<K>{sb});
+                merge_levels_pow2<NT, E>(SKeys<K, W>{sb});
             } else if (ALIGNED) {
-                merge_pieces_aligned<NT, E>(SKeys<K>{sb}, off, Kr, (int)tot);
+                merge_pieces_aligned<NT, E>(SKeys<K, W>{sb}, off, Kr, (int)tot);
             } else {
-                merge_pieces<NT, E>(SKeys<K>{sb}, off, Kr, (int)take);
+                merge_pieces<NT, E>(SKeys<K, W>{sb}, off, Kr, (int)take);
             }
             for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
             out += take;

@@ -18,7 +18,7 @@ template <> struct Cfg<uint32_t> {
     static constexpr int TNT = 256, TE = 32, MNT = 512, ME = 32, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<uint64_t> {
-    static constexpr int TNT = 256, TE = 32, MNT = 512, ME = 16, PNT = 1024, PE = 8;
+    static constexpr int TNT = 256, TE = 32, MNT = 256, ME = 32, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<Rec> {
     static constexpr int TNT = 256, TE = 16, MNT = 1024, ME = 8, PNT = 512, PE = 8;
@@ -234,8 +234,14 @@ template <typename K> struct Pipeline {
         return STagged<K>::bytes(POOL) + 4 * (size_t)POOL + 4 * (size_t)(POOL / 2 + 1) + 4 * (size_t)(Kr + 1) + 64;
     }
     static constexpr int BE = ME / 2;  // keys per thread of the oversized-group path
-    static size_t merge_smem(int Kr) { return SBuf<K>::bytes(CAP) + 16 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
-    static size_t big_smem(int Kr) { return SBuf<K>::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64; }
+    static size_t merge_smem(int Kr)
+    {
+        return SBuf<K, TilePad<K, ME>::v>::bytes(CAP) + 16 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64;
+    }
+    static size_t big_smem(int Kr)
+    {
+        return SBuf<K, TilePad<K, BE>::v>::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64;
+    }
     static size_t tile_smem() { return SBuf<K, TilePad<K, TE>::v>::bytes(T) + 64; }
 
     static Inst inst_of(const Plan<K>& pl, const SortArgs& a)
