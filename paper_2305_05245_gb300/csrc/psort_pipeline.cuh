@@ -21,7 +21,7 @@ template <> struct Cfg<uint64_t> {
     static constexpr int TNT = 256, TE = 32, MNT = 256, ME = 32, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<Rec> {
-    static constexpr int TNT = 256, TE = 16, MNT = 1024, ME = 8, PNT = 512, PE = 8;
+    static constexpr int TNT = 256, TE = 16, MNT = 256, ME = 16, PNT = 512, PE = 8;
 };
 
 constexpr int64_t FMAX = 256;  // largest fan-in of one in-block merge pass
