@@ -133,12 +133,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2305_05245_gb300", "csrc")
+    src = "".join(open(os.path.join(csrc, f)).read() for f in ("psort_kernels.cuh", "psort_pipeline.cuh"))
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def ncu_traffic(kernel: str, workload: str):
     """dram bytes per launch recorded in profiles/ncu_traffic.json for this
-    kernel and workload (null when absent or stale)."""
+    kernel and workload; null when absent, or when the kernel sources changed
+    since the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)
+        if d.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
         e = d.get(workload, {}).get(kernel)
         return None if e is None else e.get("dram_bytes_per_launch")
     except Exception:
