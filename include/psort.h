@@ -160,9 +160,13 @@ int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dt
                   ps_stream_t stream);
 
 /* End-to-end form for callers whose keys live in HOST memory (pinned or
- * pageable): copies the n keys to the device, sorts them as ps_sort_ex does,
- * copies the result back into `host_keys`, and waits for `stream` to finish
- * before returning.  Device buffers come from the library's pool. */
+ * pageable; naturally aligned for the dtype): sorts them as ps_sort_ex does,
+ * leaves the result in `host_keys`, and waits for `stream` to finish before
+ * returning.  Page-locked memory the device can address (cudaHostAlloc, or
+ * cudaHostRegister with mapping, e.g. a pinned torch tensor) is read by the
+ * first pass and written by the last pass directly, with no separate copies;
+ * other memory is copied to a device buffer and back.  Device buffers come
+ * from the library's pool. */
 int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode,
                  const ps_params* params, ps_stream_t stream);
 

@@ -230,9 +230,10 @@ def autotune_set(dtype, log2_n: int, n_blocks: int, n_parts: int, batched: bool 
 
 
 def sort_host(arr, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, stream=None) -> None:
-    """Sort a host array in place through ps_sort_host (copies to the device,
-    sorts, copies back, waits).  ``arr`` is a contiguous numpy array or a CPU
-    torch tensor (pinned memory gives the fastest copies)."""
+    """Sort a host array in place through ps_sort_host and wait.  ``arr`` is a
+    contiguous numpy array or a CPU torch tensor; pinned (page-locked) memory
+    is read and written by the sort's first and last passes directly, other
+    memory is copied to the device and back."""
     lib = _lib.load()
     import numpy as np
     if isinstance(arr, np.ndarray):

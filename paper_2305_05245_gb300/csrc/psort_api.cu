@@ -568,13 +568,45 @@ int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode, const ps
     if (!host_keys) return PS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)n * dtype_size(dtype);
+    if ((uintptr_t)host_keys % dtype_size(dtype) != 0) return PS_ERR_INVALID_ARG;
+    // Page-locked host memory that the device can address directly (mapped
+    // pinned memory; on GB300 it travels over NVLink-C2C): the first pass
+    // reads the keys from it and the last pass writes the result back into
+    // it, so the transfers ride inside the tile sort and the final merge
+    // instead of two separate copies.  Other host memory is copied in and out.
+    cudaPointerAttributes pa;
+    void* mapped = nullptr;
+    if (cudaPointerGetAttributes(&pa, host_keys) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr)
+        mapped = pa.devicePointer;
+    cudaGetLastError();  // a pageable pointer may leave an error behind on older drivers
     void* d = nullptr;
     rc = ws_alloc(&d, bytes, s);
     if (rc != PS_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(d, host_keys, bytes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        rc = sort_common(d, nullptr, n, dtype, pivot_mode, params, nullptr, stream);
-        if (rc == PS_OK) e = cudaMemcpyAsync(host_keys, d, bytes, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaSuccess;
+    if (mapped) {
+        ps_params r;
+        resolve(n, dtype, params, &r);
+        SortArgs a;
+        a.keys = d;
+        a.payload = nullptr;
+        a.n = n;
+        a.dtype = dtype;
+        a.mode = pivot_mode;
+        a.n_B = r.n_blocks;
+        a.n_P = r.n_parts;
+        a.merge_variant = (int)r.merge_variant;
+        a.trace = nullptr;
+        a.stream = s;
+        a.src_keys = mapped;
+        a.dst_keys = mapped;
+        rc = dispatch(a);
+    } else {
+        e = cudaMemcpyAsync(d, host_keys, bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            rc = sort_common(d, nullptr, n, dtype, pivot_mode, params, nullptr, stream);
+            if (rc == PS_OK) e = cudaMemcpyAsync(host_keys, d, bytes, cudaMemcpyDeviceToHost, s);
+        }
     }
     ws_free(d, s);
     if (e != cudaSuccess) return fail_cuda(e);

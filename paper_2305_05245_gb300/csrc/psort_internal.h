@@ -32,6 +32,12 @@ struct SortArgs {
     int64_t n_max = 0;   // longest instance
     int64_t n_sum = 0;   // keys over all instances
     int64_t extent = 0;  // extent of the key arrays (largest end offset)
+    // Optional separate ends of a keys-only sort: the first pass reads src_keys
+    // and the last pass writes dst_keys (n keys each, any memory the device
+    // can address, e.g. mapped pinned host memory); `keys` is then device
+    // scratch for the passes in between.  nullptr: both are `keys`.
+    const void* src_keys = nullptr;
+    void* dst_keys = nullptr;
 };
 
 // Workspace from the library's stream-ordered pool.

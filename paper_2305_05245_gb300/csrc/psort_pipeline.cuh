@@ -205,6 +205,19 @@ template <> inline GBuf<uint32_t> gbuf_user<uint32_t>(const SortArgs& a) { retur
 template <> inline GBuf<uint64_t> gbuf_user<uint64_t>(const SortArgs& a) { return GBuf<uint64_t>{(uint64_t*)a.keys, user_extent(a)}; }
 template <> inline GBuf<Rec> gbuf_user<Rec>(const SortArgs& a) { return GBuf<Rec>{(uint64_t*)a.keys, a.payload, user_extent(a)}; }
 
+// A keys-only buffer at p (the separate first-pass source / last-pass
+// destination of SortArgs); records never take this path.
+template <typename K> static GBuf<K> gbuf_ext(const void* p, const GBuf<K>& fallback);
+template <> inline GBuf<uint32_t> gbuf_ext<uint32_t>(const void* p, const GBuf<uint32_t>& f)
+{
+    return p ? GBuf<uint32_t>{(uint32_t*)p, f.n} : f;
+}
+template <> inline GBuf<uint64_t> gbuf_ext<uint64_t>(const void* p, const GBuf<uint64_t>& f)
+{
+    return p ? GBuf<uint64_t>{(uint64_t*)p, f.n} : f;
+}
+template <> inline GBuf<Rec> gbuf_ext<Rec>(const void*, const GBuf<Rec>& f) { return f; }
+
 template <typename K> static bool same_buf(const GBuf<K>& x, const GBuf<K>& y);
 template <> inline bool same_buf<uint32_t>(const GBuf<uint32_t>& x, const GBuf<uint32_t>& y) { return x.p == y.p; }
 template <> inline bool same_buf<uint64_t>(const GBuf<uint64_t>& x, const GBuf<uint64_t>& y) { return x.p == y.p; }
@@ -360,6 +373,8 @@ template <typename K> struct Pipeline {
         cudaStream_t s = a.stream;
         GBuf<K> user = gbuf_user<K>(a);
         GBuf<K> wsb = gbuf_at<K>(ws + pl.o_data, pl.N);
+        const GBuf<K> first = gbuf_ext<K>(a.src_keys, user);  // read by the first pass
+        const GBuf<K> last = gbuf_ext<K>(a.dst_keys, user);   // written by the last pass
         const Inst in = inst_of(pl, a);
         cudaError_t e;
         // Step 1: sort each block (tiles, then in-block merge passes).  The
@@ -368,7 +383,8 @@ template <typename K> struct Pipeline {
         // it is the whole sort (one block, one partition).
         const bool end_in_user = pl.direct;
         GBuf<K> cur = ((pl.npass % 2 == 0) != end_in_user) ? wsb : user;
-        if ((e = tile_sort<XF>(user, cur, pl, a, s)) != cudaSuccess) return e;
+        if (end_in_user && pl.npass == 0) cur = last;
+        if ((e = tile_sort<XF>(first, cur, pl, a, s)) != cudaSuccess) return e;
         int64_t W = T;
         for (int p = 0; p < pl.npass; p++) {
             MergeJob job{};  // in-block pass p
@@ -381,6 +397,7 @@ template <typename K> struct Pipeline {
             const int64_t Rp = (pl.L + W - 1) / W;
             job.gpb = (Rp + pl.F[p] - 1) / pl.F[p];
             GBuf<K> nxt = same_buf(cur, wsb) ? user : wsb;
+            if (p + 1 == pl.npass && end_in_user) nxt = last;
             if (p + 1 == pl.npass && end_in_user) {
                 if ((e = merge<XF>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) return e;
             } else if ((e = merge<0>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) {
@@ -442,7 +459,7 @@ template <typename K> struct Pipeline {
         job.splits = splits;
         job.offsets = offs;
         job.n_P = pl.n_P;
-        if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, user, pl, ws, s, a.merge_variant)) != cudaSuccess) return e;
+        if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, last, pl, ws, s, a.merge_variant)) != cudaSuccess) return e;
         // Trace (single sorts only).
         if (a.trace && pl.n_inst == 1) {
             const ps_trace* t = a.trace;
