@@ -288,14 +288,16 @@ int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode,
     for (int64_t i = 0; i < n_segs; i++)
         if (off[i + 1] < off[i]) return PS_ERR_INVALID_ARG;
     const int64_t extent = off[(size_t)n_segs];
-    // bins: 0 = fits one tile (one CTA each); b >= 1 = lengths in (T*2^(b-1), T*2^b]
+    // bins: 0 = at most SMALL_SEG keys (one small CTA each); 1 = fits one
+    // tile (one tile-sort CTA each); b >= 2 = lengths in (T*2^(b-2), T*2^(b-1)]
     const int64_t tile = 8192;
     std::vector<std::vector<int64_t>> bins(48);
     for (int64_t i = 0; i < n_segs; i++) {
         const int64_t len = off[i + 1] - off[i];
         if (len <= 1) continue;
-        int b = 0;
-        while (len > (tile << b)) b++;
+        int b = 1;
+        if (len <= SMALL_SEG) b = 0;
+        while (len > (tile << (b - 1)) && b > 0) b++;
         bins[b].push_back(i);
     }
     // one device array holds every bin's (start, length) pairs
@@ -340,7 +342,7 @@ int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode,
         }
         ps_params r;
         memset(&r, 0, sizeof(r));
-        if (b == 0) {
+        if (b <= 1) {
             r.n_blocks = r.n_parts = 1;  // one tile: the block sort is the whole sort
         } else if (force) {
             r = *force;
@@ -363,7 +365,8 @@ int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode,
         a.n_max = nmax;
         a.n_sum = nsum;
         a.extent = extent;
-        rc = dispatch(a);
+        if (b == 0) rc = narrow ? run_small_u32(a) : run_small_u64(a);
+        else rc = dispatch(a);
     }
     ws_free(dev, s);
     return rc;

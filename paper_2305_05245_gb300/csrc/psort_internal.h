@@ -89,5 +89,9 @@ size_t sort_ws_bytes(int64_t n, int dtype);
 // The same sorts on a caller-provided workspace (allocation-free entry point).
 int run_sort_u32_on(const SortArgs& a, char* ws, size_t cap);
 int run_sort_u64_on(const SortArgs& a, char* ws, size_t cap);
+// Batches of instances of at most 1024 keys each: one small CTA per instance.
+int run_small_u32(const SortArgs& a);
+int run_small_u64(const SortArgs& a);
+constexpr int64_t SMALL_SEG = 1024;
 
 }  // namespace ps

@@ -497,6 +497,37 @@ template <typename K> struct Pipeline {
             pl.make(a.n, 1, a.n, a.n, a.n_B, a.n_P, a.mode);
     }
 
+    // Small instances (every one at most SNT * SE keys, n_B = n_P = 1): one
+    // small CTA sorts each instance in shared memory and writes the result.
+    static constexpr int SNT = 64, SE = 16;
+    static int run_small(const SortArgs& a)
+    {
+        cudaError_t e;
+        switch (xf_of(a.dtype)) {
+        case 1: e = small_xf<1>(a); break;
+        case 2: e = small_xf<2>(a); break;
+        default: e = small_xf<0>(a); break;
+        }
+        return e == cudaSuccess ? PS_OK : fail_cuda(e);
+    }
+    template <int XF> static cudaError_t small_xf(const SortArgs& a)
+    {
+        if (a.n_max > SNT * SE) return cudaErrorInvalidValue;
+        auto f = k_tile_sort<SNT, SE, K, XF, true>;
+        const size_t sm = SBuf<K, TilePad<K, SE>::v>::bytes(SNT * SE) + 64;
+        cudaError_t e = smem_attr(f, sm);
+        if (e != cudaSuccess) return e;
+        Inst in;
+        in.base = a.inst_base;
+        in.n = a.inst_n;
+        in.count = a.n_inst;
+        in.n0 = a.n_max;
+        GBuf<K> user = gbuf_user<K>(a);
+        ProfScope ps_("small_sort", a.stream);
+        f<<<(unsigned)a.n_inst, SNT, sm, a.stream>>>(user, user, in, 1, 1);
+        return cudaGetLastError();
+    }
+
     static int run(const SortArgs& a)
     {
         Plan<K> pl;

@@ -47,7 +47,7 @@ def to_dev(a):
     return torch.from_numpy(a.copy()).cuda()
 
 
-SPECIAL = [0, 1, 2, 8191, 8192, 8193, 16385, 70_000, 300_001, 1 << 20]
+SPECIAL = [0, 1, 2, 1023, 1024, 1025, 8191, 8192, 8193, 16385, 70_000, 300_001, 1 << 20]
 
 
 @pytest.mark.parametrize("dtype,dist", [("int32", "uniform"), ("int64", "few_unique"),
@@ -86,6 +86,23 @@ def test_batch_equals_per_segment_sort(ps):
             ps.sort(seg, "exact")
     torch.cuda.synchronize()
     assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("dtype", ["int32", "float64"])
+def test_batch_many_tiny_segments(ps, ora, dtype):
+    """100,000 segments of 2..64 keys (the small-segment bin: one small CTA
+    per segment) plus a few at the bin edges."""
+    import torch
+    z = synth.splitmix64(synth.seed_for("tiny", dtype), 100_000)
+    lens = (2 + (z % np.uint64(63))).astype(np.int64)
+    lens[:4] = [1024, 1025, 1, 0]
+    offs = np.zeros(len(lens) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    keys = synth.keys(int(offs[-1]), dtype, "few_unique", seed=synth.seed_for("tiny-keys", dtype))
+    x = to_dev(keys)
+    ps.sort_batch(x, torch.from_numpy(offs).cuda(), "exact")
+    torch.cuda.synchronize()
+    assert x.cpu().numpy().tobytes() == reference(ora, keys, offs).tobytes()
 
 
 def test_batch_config4_shape(ps, ora):
