@@ -743,7 +743,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_chunk_plan(Level L, int64_t cnom, int64_t jcap, int64_t* choff)
 {
     const int64_t G = *L.ng < L.cap ? *L.ng : L.cap;
-    PS_IN(*L.ng, L.cap + 1, 21);
+    (void)PS_IN(*L.ng, L.cap + 1, 21);
     int64_t carry = 0;
     for (int64_t base = 0; base < G; base += NT) {
         const int64_t g = base + threadIdx.x;
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* chof
     const int64_t c = blockIdx.x;
     const int64_t ng = *L.ng < L.cap ? *L.ng : L.cap;
     int64_t nch = choff[ng];
-    PS_IN(nch, C.cap + 1, 29);
+    (void)PS_IN(nch, C.cap + 1, 29);
     if (nch > C.cap) nch = C.cap;
     if (c >= nch) return;
     const int Kr = L.K;
@@ -987,7 +987,7 @@ __global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* chof
     for (int r = threadIdx.x; r < Kr; r += NT) {
         const int64_t lo = C.lo[c * Kr + r];
         int64_t hi = last ? L.hi[g * Kr + r] : C.lo[(c + 1) * Kr + r];
-        PS_IN(hi - lo, INT64_MAX, 34);  // siblings' windows must not run backwards
+        (void)PS_IN(hi - lo, INT64_MAX, 34);  // siblings' windows must not run backwards
         if (hi < lo) hi = lo;
         C.hi[c * Kr + r] = hi;
         before += lo - L.lo[g * Kr + r];
@@ -1016,7 +1016,7 @@ __device__ K select_value(const GBuf<K>& src, const int64_t* a, const int64_t* b
 {
     using U = typename KT<K>::U;
     U lo = 0, hi = KT<K>::umax();
-    PS_IN(nruns, NT * MAXPER + 1, 38);  // more runs than the register windows hold
+    (void)PS_IN(nruns, NT * MAXPER + 1, 38);  // more runs than the register windows hold
     const int per = (nruns + NT - 1) / NT;
     const int r0 = threadIdx.x * per;
     int64_t wa[MAXPER], wb[MAXPER];
