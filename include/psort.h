@@ -233,6 +233,14 @@ int ps_server_submit(ps_server* server, void* dev_keys, int64_t n, int dtype, in
 int ps_server_poll(ps_server* server, uint64_t* done_ids, int* statuses, int cap, int* n_done);
 int ps_server_close(ps_server* server);
 
+/* Failure injection for tests, on the host (no device fault): what = 0 makes
+ * the next `count` admitted rounds fail at launch (their requests complete
+ * with PS_ERR_CUDA, nothing is queued on the GPU); what = 1 retires the next
+ * `count` idle stream slots as if their streams had failed (the server keeps
+ * serving on the others; with none left, queued and new requests complete
+ * with PS_ERR_CUDA).  PS_ERR_INVALID_ARG for other values. */
+int ps_server_debug_fail(ps_server* server, int what, int count);
+
 /* ---- allocation-free variant -------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory: code running while a CUDA graph is

@@ -341,6 +341,12 @@ class Server:
             self._keep.pop(rid, None)
         return out
 
+    def debug_fail(self, what: str, count: int = 1) -> None:
+        """Host-side failure injection (ps_server_debug_fail): "rounds" fails the
+        next admitted rounds at launch, "streams" retires idle stream slots."""
+        code = {"rounds": 0, "streams": 1}[what]
+        _lib.check(self._lib, "ps_server_debug_fail", self._lib.ps_server_debug_fail(self._h, code, count))
+
     def close(self) -> None:
         if self._h:
             _lib.check(self._lib, "ps_server_close", self._lib.ps_server_close(self._h))

@@ -77,6 +77,10 @@ struct Server {
     uint64_t next_id = 1;
     Slot slots[NSLOT];
     std::thread worker;
+    // host-side failure injection (ps_server_debug_fail): rounds to fail at
+    // launch, and idle slots to retire as if their streams had failed
+    int fail_rounds = 0;
+    int kill_slots = 0;
 
     // Retire a round once: from its stream's host callback (no CUDA calls
     // there), or from the worker when the stream reports an error.
@@ -105,6 +109,14 @@ struct Server {
         Slot& sl = slots[r->slot];
         cudaStream_t st = sl.stream;
         int rc = PS_OK;
+        bool inject = false;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (fail_rounds > 0) {
+                fail_rounds--;
+                inject = true;
+            }
+        }
         // one pinned table for the whole round (2 int64 per request); every
         // group stages its instance table in its own part of it, and the slot
         // reuses it only after the round has retired
@@ -117,6 +129,7 @@ struct Server {
             else sl.pinned = nullptr;
         }
         size_t pin_at = 0;
+        if (inject) rc = PS_ERR_CUDA;  // as if a launch had failed: nothing is queued
         // group by (dtype, mode): each group is one batched sort
         std::vector<bool> taken(r->reqs.size(), false);
         for (size_t i = 0; i < r->reqs.size() && rc == PS_OK; i++) {
@@ -196,6 +209,10 @@ struct Server {
             int slot = -1;
             int live = 0;
             for (int i = 0; i < NSLOT; i++) {
+                if (!slots[i].dead && !slots[i].busy && kill_slots > 0) {
+                    slots[i].dead = true;  // injected stream failure of an idle slot
+                    kill_slots--;
+                }
                 if (slots[i].dead) continue;
                 live++;
                 if (!slots[i].busy && slot < 0) slot = i;
@@ -303,6 +320,19 @@ int ps_server_poll(ps_server* p, uint64_t* done_ids, int* statuses, int cap, int
     }
     s.done.erase(s.done.begin(), s.done.begin() + k);
     *n_done = k;
+    return PS_OK;
+}
+
+int ps_server_debug_fail(ps_server* p, int what, int count)
+{
+    if (!p || count < 0 || (what != 0 && what != 1)) return PS_ERR_INVALID_ARG;
+    Server& s = p->s;
+    {
+        std::lock_guard<std::mutex> lk(s.mu);
+        if (what == 0) s.fail_rounds += count;
+        else s.kill_slots += count;
+    }
+    s.cv.notify_all();
     return PS_OK;
 }
 

@@ -130,3 +130,61 @@ def test_server_budget_and_close_drains(ps):
     torch.cuda.synchronize()
     for w, y in zip(work, want):
         assert torch.equal(w, y)
+
+
+def test_server_failed_round_does_not_stop_the_others(ps):
+    """A round that fails at launch (injected on the host) completes its
+    requests with an error status, leaves their keys untouched, and the
+    server goes on serving correctly."""
+    import torch
+    reqs = make_requests(40, 5, max_log=18)
+    want = alone(ps, reqs)
+    work = [x.clone() for x, _ in reqs]
+    torch.cuda.synchronize()
+    srv = ps.Server(budget_bytes=8 << 30, max_inflight=1)  # one request per round
+    try:
+        srv.debug_fail("rounds", 3)
+        ids = [srv.submit(w, mode) for w, (_, mode) in zip(work, reqs)]
+        got = wait_all(srv, ids)
+    finally:
+        srv.close()
+    torch.cuda.synchronize()
+    failed = [i for i, rid in enumerate(ids) if got[rid] != 0]
+    # the first three admitted rounds (one request of more than one key each) fail
+    multi = [i for i, (x, _) in enumerate(reqs) if x.numel() > 1]
+    assert failed == multi[:3]
+    for i, (w, (x, _)) in enumerate(zip(work, reqs)):
+        if i in failed:
+            assert torch.equal(w, x), "a failed request's keys changed"
+        else:
+            assert got[ids[i]] == 0 and torch.equal(w, want[i])
+
+
+def test_server_survives_failed_streams(ps):
+    """Two of the three stream slots retired (injected): results stay exact on
+    the last one.  All three retired: queued and new requests fail with
+    PS_ERR_CUDA and close still returns."""
+    import torch
+    reqs = make_requests(30, 9, max_log=18)
+    want = alone(ps, reqs)
+    work = [x.clone() for x, _ in reqs]
+    torch.cuda.synchronize()
+    srv = ps.Server(budget_bytes=8 << 30, max_inflight=8)
+    try:
+        srv.debug_fail("streams", 2)
+        ids = [srv.submit(w, mode) for w, (_, mode) in zip(work, reqs)]
+        got = wait_all(srv, ids)
+        assert all(got[r] == 0 for r in ids)
+        for w, y in zip(work, want):
+            assert torch.equal(w, y)
+        srv.debug_fail("streams", 1)
+        time.sleep(0.2)
+        x = synth.keys_torch(100_000, "int64", "uniform", seed=3)
+        before = x.clone()
+        rid = srv.submit(x, "exact")
+        got = wait_all(srv, [rid])
+        assert got[rid] == -4  # PS_ERR_CUDA
+        torch.cuda.synchronize()
+        assert torch.equal(x, before)
+    finally:
+        srv.close()
