@@ -156,3 +156,43 @@ def test_records_2p28(ps):
     rk = (kk * N) // n_P
     assert torch.equal(tr.offsets[1:-1], rk)
     assert torch.equal(tr.pivots[: n_P - 1], k[rk - 1]) and torch.equal(tr.pivot_payload[: n_P - 1], p[rk - 1])
+
+
+def _multiset_hash(t):
+    """Order-independent 64-bit hash of a tensor's values (sum of SplitMix64
+    finalisers of the bit patterns, wrapping), in chunks."""
+    import torch
+    acc = torch.zeros((), dtype=torch.int64, device=t.device)
+    bits = t.view(torch.int32) if t.element_size() == 4 else t.view(torch.int64)
+    for lo in range(0, t.numel(), 1 << 27):
+        z = bits[lo:lo + (1 << 27)].to(torch.int64)
+        acc = acc + synth._mix_t(z * -7046029254386353131 + 1).sum()
+    return int(acc)
+
+
+@pytest.mark.parametrize("dtype", ["int32", "int64"])
+def test_beyond_2p31_keys(ps, dtype):
+    """N = 2^31 + 12,345 keys (element indices beyond 32 bits), exact splitting
+    with automatic parameters: non-decreasing, the same multiset, and the
+    partition offsets of Eq. 1."""
+    import torch
+    n = (1 << 31) + 12_345
+    _INPUTS.clear()
+    torch.cuda.empty_cache()
+    x = synth.keys_torch(n, dtype, "uniform", seed=synth.seed_for("2p31", dtype))
+    h0 = _multiset_hash(x)
+    code = 0 if dtype == "int32" else 1
+    nb, np_ = ps.resolve_params(n, code)
+    tr = ps.sort(x, "exact", n_blocks=nb, n_parts=np_, trace=True)
+    torch.cuda.synchronize()
+    ok = True
+    for lo in range(0, n - 1, 1 << 28):
+        seg = x[lo:min(n, lo + (1 << 28) + 1)]
+        ok = ok and bool((seg[1:] >= seg[:-1]).all())
+    assert ok, "output is not non-decreasing"
+    assert _multiset_hash(x) == h0, "output is not a permutation of the input"
+    k = torch.arange(1, np_, device=x.device, dtype=torch.int64)
+    assert torch.equal(tr.offsets[1:-1], (k * n) // np_)
+    assert int(tr.offsets[-1]) == n
+    del x, tr
+    torch.cuda.empty_cache()
