@@ -159,6 +159,21 @@ int ps_sort_struct(void* records, int64_t n, int64_t record_bytes, int64_t key_o
 int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dtype, int pivot_mode,
                   ps_stream_t stream);
 
+/* Batch plans for repeated batches of one shape.  ps_batch_plan_create reads
+ * n_segs+1 HOST offsets once, bins the segments as ps_sort_batch does, and
+ * allocates (cudaMalloc) the device instance table and the workspace of the
+ * largest bin; it waits for those copies.  ps_batch_run then queues the sort
+ * of every segment of `keys` (device memory laid out as the offsets say, the
+ * dtype and pivot mode of the plan) on `stream` with no host synchronisation
+ * and no allocation, so a caller can capture it in a CUDA graph and replay it.
+ * Runs of one plan share its workspace: they must not overlap on the GPU.
+ * Results equal ps_sort on each segment alone. */
+typedef struct ps_batch_plan ps_batch_plan;
+int ps_batch_plan_create(const int64_t* host_seg_offsets, int64_t n_segs, int dtype, int pivot_mode,
+                         ps_batch_plan** out);
+int ps_batch_run(const ps_batch_plan* plan, void* keys, ps_stream_t stream);
+int ps_batch_plan_destroy(ps_batch_plan* plan);
+
 /* End-to-end form for callers whose keys live in HOST memory (pinned or
  * pageable; naturally aligned for the dtype): sorts them as ps_sort_ex does,
  * leaves the result in `host_keys`, and waits for `stream` to finish before

@@ -18,7 +18,7 @@ from ._lib import PS_PIVOT_EXACT, PS_PIVOT_REGULAR, PsortError  # noqa: F401
 
 __all__ = ["sort", "sort_pairs", "sort_host", "resolve_params", "workspace_bytes", "Trace",
            "PsortError", "PS_PIVOT_EXACT", "PS_PIVOT_REGULAR", "profile_enable", "profile_read",
-           "profile_reset", "sort_noalloc", "sort_batch", "sort_struct", "Server", "autotune",
+           "profile_reset", "sort_noalloc", "sort_batch", "sort_struct", "Server", "BatchPlan", "autotune",
            "autotune_table", "autotune_set"]
 
 _MODES = {"regular": _lib.PS_PIVOT_REGULAR, "psrs": _lib.PS_PIVOT_REGULAR, 0: 0,
@@ -298,6 +298,48 @@ def sort_batch(keys, seg_offsets, pivot_mode="exact", stream=None) -> None:
     rc = lib.ps_sort_batch(seg_offsets.data_ptr(), n_segs, keys.data_ptr() if keys.numel() else None,
                            _dtype_code(keys.dtype), _mode(pivot_mode), _stream_handle(stream))
     _lib.check(lib, "ps_sort_batch", rc)
+
+
+class BatchPlan:
+    """A batch shape planned once (ps_batch_plan_create): ``run`` sorts every
+    segment of a key tensor laid out by the same offsets with no host
+    synchronisation or allocation, so it can be captured in a CUDA graph.
+
+        plan = BatchPlan(offsets_numpy_int64, torch.int32, "exact")
+        plan.run(keys)                       # or inside torch.cuda.graph(...)
+        plan.close()"""
+
+    def __init__(self, seg_offsets, dtype, pivot_mode="exact"):
+        import numpy as np
+        self._lib = _lib.load()
+        off = np.ascontiguousarray(np.asarray(seg_offsets, dtype=np.int64))
+        self._code = _code_of(dtype)
+        h = ctypes.c_void_p()
+        _lib.check(self._lib, "ps_batch_plan_create",
+                   self._lib.ps_batch_plan_create(off.ctypes.data if off.size else None, max(off.size - 1, 0),
+                                                  self._code, _mode(pivot_mode), ctypes.byref(h)))
+        self._h = h
+        self.extent = int(off[-1]) if off.size else 0
+
+    def run(self, keys, stream=None) -> None:
+        if not keys.is_cuda or keys.dim() != 1 or not keys.is_contiguous():
+            raise ValueError("keys must be a contiguous 1-D CUDA tensor")
+        if keys.element_size() != (4 if self._code in (0, 2, 4) else 8):
+            raise ValueError("keys do not have the plan's key width")
+        if keys.numel() < self.extent:
+            raise ValueError("keys are shorter than the planned segments")
+        _lib.check(self._lib, "ps_batch_run", self._lib.ps_batch_run(self._h, keys.data_ptr(), _stream_handle(stream)))
+
+    def close(self) -> None:
+        if self._h:
+            _lib.check(self._lib, "ps_batch_plan_destroy", self._lib.ps_batch_plan_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -273,21 +273,36 @@ size_t sort_ws_bytes(int64_t n, int dtype)
     }
 }
 
-// Batched sort of the segments [off[i], off[i+1]) of `keys` (host offsets):
-// bins by length, one multi-instance pipeline per bin, queued on s.
-int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
-               int64_t* pinned, size_t pinned_cap, const ps_params* force)
+// Batched sorts.  A batch plan bins the segments [off[i], off[i+1]) by length
+// and fixes each bin's parameters and its part of the instance table (per
+// bin: all starts, then all lengths); launching a plan queues one
+// multi-instance pipeline per bin.
+struct BatchBin {
+    size_t at;                // offset of the bin's starts in the instance table
+    int64_t cnt, nmax, nsum;  // instances, longest, total keys
+    int64_t n_B, n_P;
+    bool small;               // at most SMALL_SEG keys each: one small CTA per segment
+};
+struct BatchPlan {
+    int dtype = 0, mode = 0;
+    int64_t extent = 0;
+    std::vector<int64_t> table;  // host copy of the instance table
+    std::vector<BatchBin> bins;
+};
+
+static int batch_make_plan(const std::vector<int64_t>& off, int dtype, int mode, const ps_params* force,
+                           BatchPlan* bp)
 {
     const int64_t n_segs = (int64_t)off.size() - 1;
-    if (n_segs <= 0) return PS_OK;
     if (dtype < PS_I32 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
-    if (!keys) return PS_ERR_INVALID_ARG;
-    const bool narrow = dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32;
-    if ((uintptr_t)keys % (narrow ? 4 : 8) != 0) return PS_ERR_INVALID_ARG;
-    if (off[0] < 0) return PS_ERR_INVALID_ARG;
+    if (n_segs < 0 || off.empty() || off[0] < 0) return PS_ERR_INVALID_ARG;
     for (int64_t i = 0; i < n_segs; i++)
         if (off[i + 1] < off[i]) return PS_ERR_INVALID_ARG;
-    const int64_t extent = off[(size_t)n_segs];
+    bp->dtype = dtype;
+    bp->mode = mode;
+    bp->extent = off[(size_t)n_segs];
+    bp->table.clear();
+    bp->bins.clear();
     // bins: 0 = at most SMALL_SEG keys (one small CTA each); 1 = fits one
     // tile (one tile-sort CTA each); b >= 2 = lengths in (T*2^(b-2), T*2^(b-1)]
     const int64_t tile = 8192;
@@ -300,45 +315,18 @@ int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode,
         while (len > (tile << (b - 1)) && b > 0) b++;
         bins[b].push_back(i);
     }
-    // one device array holds every bin's (start, length) pairs
-    size_t total = 0;
-    for (auto& v : bins) total += v.size();
-    if (total == 0) return PS_OK;
-    // the instance table is staged in the caller's pinned buffer when it is
-    // large enough (the copy then stays asynchronous; the caller keeps the
-    // buffer untouched until the stream has passed this point), else in a
-    // local array that must outlive the copy, so the call waits for it
-    std::vector<int64_t> local;
-    int64_t* host = nullptr;
-    if (pinned && pinned_cap >= 2 * total) {
-        host = pinned;
-    } else {
-        local.resize(2 * total);
-        host = local.data();
-    }
-    void* dev = nullptr;
-    int rc = ws_alloc(&dev, 2 * total * 8, s);
-    if (rc != PS_OK) return rc;
-    size_t pos = 0;
-    std::vector<size_t> at(bins.size());
     for (size_t b = 0; b < bins.size(); b++) {
-        at[b] = pos;
-        for (int64_t i : bins[b]) host[pos++] = off[i];
-        for (int64_t i : bins[b]) host[pos++] = off[i + 1] - off[i];
-    }
-    cudaError_t e = cudaMemcpyAsync(dev, host, 2 * total * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && host != pinned) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        ws_free(dev, s);
-        return fail_cuda(e);
-    }
-    for (size_t b = 0; b < bins.size() && rc == PS_OK; b++) {
-        const int64_t cnt = (int64_t)bins[b].size();
-        if (cnt == 0) continue;
-        int64_t nmax = 0, nsum = 0;
+        if (bins[b].empty()) continue;
+        BatchBin bb;
+        bb.at = bp->table.size();
+        bb.cnt = (int64_t)bins[b].size();
+        bb.nmax = bb.nsum = 0;
+        for (int64_t i : bins[b]) bp->table.push_back(off[i]);
         for (int64_t i : bins[b]) {
-            nmax = std::max<int64_t>(nmax, off[i + 1] - off[i]);
-            nsum += off[i + 1] - off[i];
+            const int64_t len = off[i + 1] - off[i];
+            bp->table.push_back(len);
+            bb.nmax = std::max<int64_t>(bb.nmax, len);
+            bb.nsum += len;
         }
         ps_params r;
         memset(&r, 0, sizeof(r));
@@ -347,27 +335,90 @@ int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode,
         } else if (force) {
             r = *force;
         } else {
-            resolve(nmax, dtype, nullptr, &r, 1);
+            resolve(bb.nmax, dtype, nullptr, &r, 1);
         }
-        SortArgs a;
-        a.keys = keys;
-        a.payload = nullptr;
-        a.n = nmax;
-        a.dtype = dtype;
-        a.mode = mode;
-        a.n_B = r.n_blocks;
-        a.n_P = r.n_parts;
-        a.trace = nullptr;
-        a.stream = s;
-        a.inst_base = (const int64_t*)dev + at[b];
-        a.inst_n = (const int64_t*)dev + at[b] + cnt;
-        a.n_inst = cnt;
-        a.n_max = nmax;
-        a.n_sum = nsum;
-        a.extent = extent;
-        if (b == 0) rc = narrow ? run_small_u32(a) : run_small_u64(a);
+        bb.n_B = r.n_blocks;
+        bb.n_P = r.n_parts;
+        bb.small = b == 0;
+        bp->bins.push_back(bb);
+    }
+    return PS_OK;
+}
+
+static SortArgs batch_bin_args(const BatchPlan& bp, const BatchBin& bb, const int64_t* dev_table, void* keys,
+                               cudaStream_t s)
+{
+    SortArgs a;
+    a.keys = keys;
+    a.payload = nullptr;
+    a.n = bb.nmax;
+    a.dtype = bp.dtype;
+    a.mode = bp.mode;
+    a.n_B = bb.n_B;
+    a.n_P = bb.n_P;
+    a.trace = nullptr;
+    a.stream = s;
+    a.inst_base = dev_table + bb.at;
+    a.inst_n = dev_table + bb.at + bb.cnt;
+    a.n_inst = bb.cnt;
+    a.n_max = bb.nmax;
+    a.n_sum = bb.nsum;
+    a.extent = bp.extent;
+    return a;
+}
+
+static bool narrow_dtype(int dtype) { return dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32; }
+
+// Queue every bin of a plan on s.  ws == nullptr: each bin takes its
+// workspace from the pool; otherwise every bin runs on ws (cap bytes) and
+// nothing is allocated.
+static int batch_launch(const BatchPlan& bp, const int64_t* dev_table, void* keys, cudaStream_t s, char* ws,
+                        size_t cap)
+{
+    const bool narrow = narrow_dtype(bp.dtype);
+    int rc = PS_OK;
+    for (size_t i = 0; i < bp.bins.size() && rc == PS_OK; i++) {
+        SortArgs a = batch_bin_args(bp, bp.bins[i], dev_table, keys, s);
+        if (bp.bins[i].small) rc = narrow ? run_small_u32(a) : run_small_u64(a);
+        else if (ws) rc = narrow ? run_sort_u32_on(a, ws, cap) : run_sort_u64_on(a, ws, cap);
         else rc = dispatch(a);
     }
+    return rc;
+}
+
+// Batched sort of the segments [off[i], off[i+1]) of `keys` (host offsets):
+// bins by length, one multi-instance pipeline per bin, queued on s.
+int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
+               int64_t* pinned, size_t pinned_cap, const ps_params* force)
+{
+    if ((int64_t)off.size() - 1 <= 0) return PS_OK;
+    if (dtype < PS_I32 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
+    if (!keys) return PS_ERR_INVALID_ARG;
+    if ((uintptr_t)keys % (narrow_dtype(dtype) ? 4 : 8) != 0) return PS_ERR_INVALID_ARG;
+    BatchPlan bp;
+    int rc = batch_make_plan(off, dtype, mode, force, &bp);
+    if (rc != PS_OK) return rc;
+    const size_t total = bp.table.size();
+    if (total == 0) return PS_OK;
+    // the instance table is staged in the caller's pinned buffer when it is
+    // large enough (the copy then stays asynchronous; the caller keeps the
+    // buffer untouched until the stream has passed this point), else the
+    // copy is waited for before the plan's host table goes away
+    const int64_t* host = bp.table.data();
+    if (pinned && pinned_cap >= total) {
+        memcpy(pinned, bp.table.data(), total * 8);
+        host = pinned;
+    }
+    void* dev = nullptr;
+    rc = ws_alloc(&dev, total * 8, s);
+    if (rc != PS_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(dev, host, total * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && host != pinned) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ws_free(dev, s);
+        return fail_cuda(e);
+    }
+    rc = batch_launch(bp, (const int64_t*)dev, keys, s, nullptr, 0);
     ws_free(dev, s);
     return rc;
 }
@@ -509,6 +560,13 @@ static int autotune(int dtype, int mode, int64_t n_min, int64_t n_max, int batch
 
 using namespace ps;
 
+struct ps_batch_plan {
+    BatchPlan plan;
+    int64_t* table = nullptr;  // device instance table
+    char* ws = nullptr;        // device workspace for the largest bin
+    size_t ws_bytes = 0;
+};
+
 extern "C" {
 
 int ps_sort(void* keys, int64_t n, int dtype, int pivot_mode, ps_stream_t stream)
@@ -558,6 +616,59 @@ int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dt
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e);
     return batch_sort(off, keys, dtype, pivot_mode, s, nullptr, 0);
+}
+
+int ps_batch_plan_create(const int64_t* host_seg_offsets, int64_t n_segs, int dtype, int pivot_mode,
+                         ps_batch_plan** out)
+{
+    if (!out) return PS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_segs < 0 || (n_segs > 0 && !host_seg_offsets)) return PS_ERR_INVALID_ARG;
+    if (dtype < PS_I32 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
+    if (pivot_mode != PS_PIVOT_REGULAR && pivot_mode != PS_PIVOT_EXACT) return PS_ERR_UNSUPPORTED;
+    std::vector<int64_t> off(host_seg_offsets, host_seg_offsets + (n_segs > 0 ? n_segs + 1 : 0));
+    if (off.empty()) off.push_back(0);
+    ps_batch_plan* p = new (std::nothrow) ps_batch_plan();
+    if (!p) return PS_ERR_NO_MEMORY;
+    int rc = batch_make_plan(off, dtype, pivot_mode, nullptr, &p->plan);
+    size_t ws = 0;
+    for (const BatchBin& bb : p->plan.bins) {
+        if (bb.small) continue;
+        SortArgs a = batch_bin_args(p->plan, bb, nullptr, nullptr, nullptr);
+        ws = std::max(ws, narrow_dtype(dtype) ? ws_bytes_args_u32(a) : ws_bytes_args_u64(a));
+    }
+    cudaError_t e = cudaSuccess;
+    if (rc == PS_OK && !p->plan.table.empty()) {
+        e = cudaMalloc((void**)&p->table, p->plan.table.size() * 8);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->table, p->plan.table.data(), p->plan.table.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && ws > 0) e = cudaMalloc((void**)&p->ws, ws);
+        p->ws_bytes = ws;
+    }
+    if (rc == PS_OK && e != cudaSuccess) rc = fail_cuda(e);
+    if (rc != PS_OK) {
+        ps_batch_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return PS_OK;
+}
+
+int ps_batch_run(const ps_batch_plan* plan, void* keys, ps_stream_t stream)
+{
+    if (!plan) return PS_ERR_INVALID_ARG;
+    if (plan->plan.table.empty()) return PS_OK;
+    if (!keys || (uintptr_t)keys % (narrow_dtype(plan->plan.dtype) ? 4 : 8) != 0) return PS_ERR_INVALID_ARG;
+    return batch_launch(plan->plan, plan->table, keys, (cudaStream_t)stream, plan->ws, plan->ws_bytes);
+}
+
+int ps_batch_plan_destroy(ps_batch_plan* plan)
+{
+    if (!plan) return PS_ERR_INVALID_ARG;
+    if (plan->table) cudaFree(plan->table);
+    if (plan->ws) cudaFree(plan->ws);
+    delete plan;
+    return PS_OK;
 }
 
 int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode, const ps_params* params, ps_stream_t stream)

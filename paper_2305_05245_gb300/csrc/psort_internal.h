@@ -93,5 +93,8 @@ int run_sort_u64_on(const SortArgs& a, char* ws, size_t cap);
 int run_small_u32(const SortArgs& a);
 int run_small_u64(const SortArgs& a);
 constexpr int64_t SMALL_SEG = 1024;
+// Workspace bytes of the sort a describes (batched instances included).
+size_t ws_bytes_args_u32(const SortArgs& a);
+size_t ws_bytes_args_u64(const SortArgs& a);
 
 }  // namespace ps

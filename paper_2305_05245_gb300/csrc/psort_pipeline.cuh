@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "psort_internal.h"
 #include "psort_kernels.cuh"
@@ -223,9 +225,40 @@ template <> inline bool same_buf<uint32_t>(const GBuf<uint32_t>& x, const GBuf<u
 template <> inline bool same_buf<uint64_t>(const GBuf<uint64_t>& x, const GBuf<uint64_t>& y) { return x.p == y.p; }
 template <> inline bool same_buf<Rec>(const GBuf<Rec>& x, const GBuf<Rec>& y) { return x.k == y.k; }
 
+// Raise a kernel's dynamic shared-memory limit once per (device, kernel) to
+// the largest size asked so far, so that launches queued later (for example
+// while a stream is being captured into a CUDA graph) make no attribute call.
+struct SmemAttrCache {
+    std::mutex mu;
+    struct Entry {
+        const void* f;
+        int dev;
+        size_t bytes;
+    };
+    std::vector<Entry> set;
+};
+inline SmemAttrCache& smem_attr_cache()
+{
+    static SmemAttrCache c;
+    return c;
+}
 template <typename KF> static cudaError_t smem_attr(KF* f, size_t bytes)
 {
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    SmemAttrCache& c = smem_attr_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    for (auto& x : c.set)
+        if (x.f == (const void*)f && x.dev == dev) {
+            if (x.bytes >= bytes) return cudaSuccess;
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            if (e == cudaSuccess) x.bytes = bytes;
+            return e;
+        }
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) c.set.push_back({(const void*)f, dev, bytes});
+    return e;
 }
 
 static inline int xf_of(int dtype)
@@ -561,6 +594,14 @@ template <typename K> struct Pipeline {
         }
         if (e != cudaSuccess) return fail_cuda(e);
         return PS_OK;
+    }
+
+    // Workspace of one (possibly multi-instance) sort as described by a.
+    static size_t ws_bytes_for(const SortArgs& a)
+    {
+        Plan<K> pl;
+        make_plan(pl, a);
+        return pl.total;
     }
 
     static size_t ws_bytes(int64_t n, int64_t nb, int64_t np)

@@ -132,3 +132,39 @@ def test_batch_argument_errors(ps):
     assert lib.ps_sort_batch(ctypes.c_void_p(bad.data_ptr()), 3, ctypes.c_void_p(x.data_ptr()), 0, 1, None) == -1
     assert lib.ps_sort_batch(None, 0, None, 0, 1, None) == 0
     assert lib.ps_sort_batch(ctypes.c_void_p(bad.data_ptr()), 3, ctypes.c_void_p(x.data_ptr()), 9, 1, None) == -2
+
+
+@pytest.mark.parametrize("dtype", ["int32", "float64"])
+def test_batch_plan_run_and_cuda_graph(ps, ora, dtype):
+    """A planned batch (ps_batch_plan_create / ps_batch_run) sorts like
+    ps_sort_batch, and the run can be captured in a CUDA graph and replayed on
+    new keys in the same buffer."""
+    import torch
+    keys, offs = make_batch(500, 18, dtype, "uniform", seed=synth.seed_for("plan", dtype) % 100000,
+                            special=SPECIAL)
+    plan = ps.BatchPlan(offs, getattr(torch, dtype), "exact")
+    try:
+        x = to_dev(keys)
+        plan.run(x)
+        torch.cuda.synchronize()
+        assert x.cpu().numpy().tobytes() == reference(ora, keys, offs).tobytes()
+        # capture one run, then replay it on two fresh inputs
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            x.copy_(to_dev(keys))
+            plan.run(x)  # warm-up on the capture stream
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.run(x)
+        for rep in range(2):
+            fresh = synth.keys(len(keys), dtype, "few_unique" if rep else "uniform",
+                               seed=synth.seed_for("plan-replay", dtype, rep))
+            x.copy_(to_dev(fresh))
+            g.replay()
+            torch.cuda.synchronize()
+            assert x.cpu().numpy().tobytes() == reference(ora, fresh, offs).tobytes()
+    finally:
+        plan.close()
