@@ -851,7 +851,7 @@ def main():
         "data": "synthetic (SplitMix64, seeded), resident in HBM",
         "config": {"workload": wl, "n": n, "dist": a.dist, "pivot": a.pivot, "n_blocks": nb,
                    "n_parts": np_, "params": "autotuned (ps_autotune, untimed)" if tuned else
-                   ("explicit" if a.n_blocks or a.n_parts else "size heuristic"),
+                   ("explicit" if a.n_blocks or a.n_parts else "library defaults (measured size table)"),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (no flush needed)",
                    "restore": "keys restored from a pristine device copy before each step, outside the timed events",

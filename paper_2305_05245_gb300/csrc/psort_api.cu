@@ -187,15 +187,49 @@ static void resolve_heuristic(int64_t n, int dtype, const ps_params* in, ps_para
 
 void resolve_default(int64_t n, int dtype, ps_params* out) { resolve_heuristic(n, dtype, nullptr, out); }
 
+// Defaults measured on GB300 with ps_autotune (exact splitting, uniform keys):
+// (n_B, n_P) per round(log2 n) from 2^14 on, for single sorts and for the size
+// bins of batched sorts, 32-bit and 64-bit keys.  Up to 2^19-2^20 keys one
+// block and one partition win (the block sort is the whole sort).
+struct DefaultTune {
+    int lo, hi;              // log2 sizes covered
+    const int32_t (*e)[2];   // e[b - lo] = {n_B, n_P}
+};
+static const int32_t kTuneU32[][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {2, 1}, {8, 8}, {16, 32},
+                                      {32, 32}, {64, 64}, {64, 128}, {128, 128}, {16, 32}, {32, 64}, {64, 128},
+                                      {64, 128}, {64, 64}};                                 // 2^14 .. 2^31
+static const int32_t kTuneU64[][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {16, 32}, {16, 16},
+                                      {32, 64}, {32, 64}, {64, 128}, {64, 128}, {16, 16}, {16, 16}, {32, 64},
+                                      {32, 64}, {64, 128}};                                 // 2^14 .. 2^30
+static const int32_t kTuneU32Batch[][2] = {{2, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {2, 1}, {8, 4},
+                                           {8, 8}, {16, 16}, {32, 16}};                    // 2^14 .. 2^24
+static const int32_t kTuneU64Batch[][2] = {{2, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}, {4, 2}, {8, 4},
+                                           {16, 8}, {32, 16}, {32, 16}};                   // 2^14 .. 2^24
+static const DefaultTune kDefaults[2][2] = {{{14, 31, kTuneU32}, {14, 30, kTuneU64}},
+                                            {{14, 24, kTuneU32Batch}, {14, 24, kTuneU64Batch}}};
+
+static bool measured_default(int ctx, int dtype, int64_t n, int32_t* nb, int32_t* np)
+{
+    const int f = tune_family(dtype);
+    if (f < 0 || n < 2) return false;
+    const DefaultTune& d = kDefaults[ctx][f];
+    const int b = tune_bin(n);
+    if (b < d.lo || b > d.hi) return false;
+    *nb = d.e[b - d.lo][0];
+    *np = d.e[b - d.lo][1];
+    return true;
+}
+
 // Automatic fields: a tuned entry for this size (context ctx) when there is
-// one, else the heuristic.  Explicit fields are kept.
+// one, else the measured default, else the heuristic.  Explicit fields are kept.
 static void resolve(int64_t n, int dtype, const ps_params* in, ps_params* out, int ctx = 0)
 {
     ps_params r;
     memset(&r, 0, sizeof(r));
     if (in) r = *in;
     int32_t nb = 0, np = 0;
-    if ((r.n_blocks <= 0 || r.n_parts <= 0) && tuned(ctx, dtype, n, &nb, &np)) {
+    if ((r.n_blocks <= 0 || r.n_parts <= 0) &&
+        (tuned(ctx, dtype, n, &nb, &np) || measured_default(ctx, dtype, n, &nb, &np))) {
         if (r.n_blocks <= 0) {
             r.n_blocks = nb;
             if (r.n_parts <= 0) r.n_parts = np;
