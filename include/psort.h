@@ -281,6 +281,11 @@ int ps_server_debug_fail(ps_server* server, int what, int count);
 #define PS_NOALLOC_SCRATCH_BYTES ((size_t)12 << 20)
 int ps_sort_noalloc(void* keys, int64_t n, int dtype, int pivot_mode, ps_stream_t stream);
 
+/* Failure injection for tests, on the host: the next `count` workspace
+ * allocations of the library fail with PS_ERR_NO_MEMORY before any CUDA call
+ * (0 turns it off).  Sorts then return PS_ERR_NO_MEMORY with nothing queued. */
+int ps_debug_fail_alloc(int count);
+
 /* ---- checked builds -------------------------------------------------------
  * A build compiled with -DPS_CHECKED (libpsort_checked.so) validates every
  * global and shared-memory index in its kernels; the first out-of-range

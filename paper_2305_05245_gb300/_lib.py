@@ -24,7 +24,7 @@ EXPORTS = ["ps_sort", "ps_sort_ex", "ps_sort_pairs", "ps_sort_host", "ps_resolve
            "ps_profile_read", "ps_profile_reset", "ps_sort_noalloc", "ps_debug_violation", "ps_sort_batch",
            "ps_server_open", "ps_server_submit", "ps_server_poll", "ps_server_close", "ps_sort_struct",
            "ps_autotune", "ps_autotune_get", "ps_autotune_set", "ps_server_debug_fail",
-           "ps_batch_plan_create", "ps_batch_run", "ps_batch_plan_destroy"]
+           "ps_batch_plan_create", "ps_batch_run", "ps_batch_plan_destroy", "ps_debug_fail_alloc"]
 
 PS_NOALLOC_MAX_KEYS = 1 << 20
 PS_STRUCT_MAX_BYTES = 4096
@@ -98,6 +98,7 @@ def load(path: str | None = None):
     lib.ps_batch_plan_create.argtypes = [vp, i64, i32, i32, ctypes.POINTER(vp)]
     lib.ps_batch_run.argtypes = [vp, vp, vp]
     lib.ps_batch_plan_destroy.argtypes = [vp]
+    lib.ps_debug_fail_alloc.argtypes = [i32]
     lib.ps_debug_violation.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.ps_profile_enable.argtypes = [i32]
     lib.ps_profile_read.argtypes = [ctypes.POINTER(PsKernelStat), i32, ctypes.POINTER(i32)]
@@ -107,7 +108,7 @@ def load(path: str | None = None):
                  "ps_profile_reset", "ps_sort_noalloc", "ps_debug_violation", "ps_sort_batch", "ps_server_open",
                  "ps_server_submit", "ps_server_poll", "ps_server_close", "ps_sort_struct", "ps_autotune",
                  "ps_autotune_get", "ps_autotune_set", "ps_server_debug_fail", "ps_batch_plan_create",
-                 "ps_batch_run", "ps_batch_plan_destroy"):
+                 "ps_batch_run", "ps_batch_plan_destroy", "ps_debug_fail_alloc"):
         getattr(lib, name).restype = i32
     if path is None:
         _lib = lib

@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -52,8 +54,14 @@ static int get_pool(cudaMemPool_t* out)
     return PS_OK;
 }
 
+// Host-side failure injection (ps_debug_fail_alloc): the next n workspace
+// allocations fail with PS_ERR_NO_MEMORY before any CUDA call.
+static std::atomic<int> g_fail_alloc{0};
+
 int ws_alloc(void** p, size_t bytes, cudaStream_t s)
 {
+    for (int k = g_fail_alloc.load(); k > 0;)
+        if (g_fail_alloc.compare_exchange_weak(k, k - 1)) return PS_ERR_NO_MEMORY;
     cudaMemPool_t pool;
     int rc = get_pool(&pool);
     if (rc != PS_OK) return rc;
@@ -248,8 +256,23 @@ static int check_params(const ps_params* p)
     return PS_OK;
 }
 
+// PS_LOG=1 in the environment: one line per sort on stderr with the
+// resolved parameters (read once).
+static int log_level()
+{
+    static const int lvl = [] {
+        const char* v = getenv("PS_LOG");
+        return v ? atoi(v) : 0;
+    }();
+    return lvl;
+}
+
 static int dispatch(SortArgs& a)
 {
+    if (log_level() >= 1)
+        fprintf(stderr, "psort: n=%lld dtype=%d mode=%d n_B=%lld n_P=%lld instances=%lld merge_variant=%d\n",
+                (long long)a.n, a.dtype, a.mode, (long long)a.n_B, (long long)a.n_P, (long long)a.n_inst,
+                a.merge_variant);
     switch (a.dtype) {
     case PS_I32: case PS_F32: case PS_U32: return run_sort_u32(a);
     case PS_I64: case PS_F64: case PS_U64: return run_sort_u64(a);
@@ -849,6 +872,13 @@ const char* ps_status_string(int status)
 }
 
 int ps_last_cuda_error(void) { return g_last_cuda; }
+
+int ps_debug_fail_alloc(int count)
+{
+    if (count < 0) return PS_ERR_INVALID_ARG;
+    g_fail_alloc.store(count);
+    return PS_OK;
+}
 
 int ps_debug_violation(uint64_t* out)
 {

@@ -110,6 +110,23 @@ def test_autotune_table_without_gpu(lib):
     assert lib.ps_autotune_get(0, 0, 40, ctypes.byref(q)) == -7
 
 
+def test_injected_allocation_failure_without_gpu(lib):
+    """An allocation failure (injected on the host) surfaces as
+    PS_ERR_NO_MEMORY from every entry point that allocates, before any device
+    work; the injection wears off after the given count."""
+    from paper_2305_05245_gb300 import _lib
+    fake = ctypes.c_void_p(0x10000)  # never touched: the sort stops at its first allocation
+    assert lib.ps_debug_fail_alloc(-1) == -1
+    assert lib.ps_debug_fail_alloc(3) == 0
+    try:
+        assert lib.ps_sort(fake, 1 << 20, 1, 1, None) == -3
+        assert lib.ps_sort_pairs(fake, fake, 1 << 20, 1, None, None, None) == -3
+        rec = ctypes.c_void_p(0x20000)
+        assert lib.ps_sort_struct(rec, 1000, 16, 0, 1, None, None) == -3
+    finally:
+        assert lib.ps_debug_fail_alloc(0) == 0
+
+
 def test_resolve_and_workspace(lib):
     import paper_2305_05245_gb300 as ps
     nb, np_ = ps.resolve_params(1 << 26, 0)
