@@ -11,9 +11,12 @@
 // on several streams, so a round admitted while earlier ones are on the GPU
 // overlaps with them.  A request's result is bit-identical to ps_sort on it
 // alone: batching changes only which launches carry it.
+#include <algorithm>
+#include <climits>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -26,7 +29,8 @@ namespace ps {
 
 namespace {
 
-constexpr int NSLOT = 3;  // rounds that may be on the GPU at once
+constexpr int NSLOT = 3;          // rounds that may be on the GPU at once
+constexpr size_t LONG_QUEUE = 16;  // queued requests beyond which rounds are not capped
 
 struct Req {
     uint64_t id;
@@ -81,6 +85,10 @@ struct Server {
     // launch, and idle slots to retire as if their streams had failed
     int fail_rounds = 0;
     int kill_slots = 0;
+    // smallest round size in keys (PS_SERVER_ROUND_KEYS in the environment
+    // overrides), and the keys waiting in the queue
+    int64_t round_keys = int64_t(1) << 23;
+    int64_t pending_keys = 0;
 
     // Retire a round once: from its stream's host callback (no CUDA calls
     // there), or from the worker when the stream reports an error.
@@ -223,6 +231,7 @@ struct Server {
                     done.push_back(Done{pending.front().id, PS_ERR_CUDA});
                     pending.pop_front();
                 }
+                pending_keys = 0;
                 if (closing && inflight == 0) break;
             }
             const bool can = slot >= 0 && !pending.empty() && inflight < max_inflight &&
@@ -237,8 +246,18 @@ struct Server {
             delete slots[slot].cur;  // retired: the slot is free
             Round* r = new Round{this, slot, {}, 0, PS_OK};
             slots[slot].cur = r;
+            // a round takes queued requests in order.  With a short queue it
+            // stops at round_keys keys (at least one request), so that small
+            // requests are not held back behind large ones; with a long queue
+            // (the GPU is saturated) it takes everything admissible, as large
+            // rounds keep the GPU busiest.
+            const int64_t cap = pending.size() > LONG_QUEUE ? INT64_MAX : round_keys;
+            int64_t keys = 0;
             while (!pending.empty() && inflight + (int)r->reqs.size() < max_inflight &&
-                   used + r->cost + pending.front().cost <= budget) {
+                   used + r->cost + pending.front().cost <= budget &&
+                   (r->reqs.empty() || keys + pending.front().n <= cap)) {
+                keys += pending.front().n;
+                pending_keys -= pending.front().n;
                 r->cost += pending.front().cost;
                 r->reqs.push_back(pending.front());
                 pending.pop_front();
@@ -273,6 +292,10 @@ int ps_server_open(size_t mem_budget_bytes, int max_inflight, ps_server** out)
     Server& s = p->s;
     s.budget = mem_budget_bytes;
     s.max_inflight = max_inflight;
+    if (const char* v = getenv("PS_SERVER_ROUND_KEYS")) {
+        const long long k = atoll(v);
+        if (k > 0) s.round_keys = k;
+    }
     cudaError_t e = cudaGetDevice(&s.dev);
     for (int i = 0; i < NSLOT && e == cudaSuccess; i++) e = cudaStreamCreateWithFlags(&s.slots[i].stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -302,7 +325,10 @@ int ps_server_submit(ps_server* p, void* dev_keys, int64_t n, int dtype, int piv
         if (cost > s.budget) return PS_ERR_BUSY;  // could never be admitted
         *req_id = s.next_id++;
         if (n <= 1) s.done.push_back(Done{*req_id, PS_OK});
-        else s.pending.push_back(Req{*req_id, dev_keys, n, dtype, pivot_mode, cost});
+        else {
+            s.pending.push_back(Req{*req_id, dev_keys, n, dtype, pivot_mode, cost});
+            s.pending_keys += n;
+        }
     }
     s.cv.notify_all();
     return PS_OK;
