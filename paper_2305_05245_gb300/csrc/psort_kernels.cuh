@@ -1011,23 +1011,32 @@ __global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* chof
 // MAXPER (enough for the largest n_B, 4096 runs, at NT threads); all threads
 // get the result.
 constexpr int MAX_RUNS = 4096;
+// The search may start from a bracket [lo0, hi0] known to hold the answer;
+// every window then starts at the elements >= lo0 and ends after those <= hi0.
 template <int NT, typename K, int MAXPER = (MAX_RUNS + NT - 1) / NT>
-__device__ K select_value(const GBuf<K>& src, const int64_t* a, const int64_t* b, int nruns, int64_t t)
+__device__ K select_value(const GBuf<K>& src, const int64_t* a, const int64_t* b, int nruns, int64_t t,
+                          typename KT<K>::U lo0 = 0, typename KT<K>::U hi0 = KT<K>::umax())
 {
     using U = typename KT<K>::U;
-    U lo = 0, hi = KT<K>::umax();
+    U lo = lo0, hi = hi0;
     (void)PS_IN(nruns, NT * MAXPER + 1, 38);  // more runs than the register windows hold
     const int per = (nruns + NT - 1) / NT;
     const int r0 = threadIdx.x * per;
     int64_t wa[MAXPER], wb[MAXPER];
+    int64_t below = 0;  // this thread's elements left of its windows
 #pragma unroll
     for (int q = 0; q < MAXPER; q++) {
         const int r = r0 + q;
         const bool ok = q < per && r < nruns;
         wa[q] = ok ? a[r] : 0;
         wb[q] = ok ? b[r] : 0;
+        if (ok && lo0 > 0) {  // elements < lo0 are below every candidate
+            const int64_t c = bound<true>(src, wa[q], wb[q], KT<K>::from_u(lo0));
+            wa[q] += c;
+            below += c;
+        }
+        if (ok && hi0 < KT<K>::umax()) wb[q] = wa[q] + bound<false>(src, wa[q], wb[q], KT<K>::from_u(hi0));
     }
-    int64_t below = 0;  // this thread's elements left of its windows
     while (lo < hi) {
         const U mid = lo + ((hi - lo) >> 1);
         const K vm = KT<K>::from_u(mid);
@@ -1391,7 +1400,37 @@ __global__ void __launch_bounds__(NT) k_pses(GBuf<K> blk, Inst in, int64_t n_B, 
         return;
     }
     const int64_t rk = (int64_t)(((unsigned __int128)k * (uint64_t)N) / (uint64_t)n_P);
-    const K v = select_value<NT, K>(blk, a, b, (int)n_B, rk > 0 ? rk : 1);
+    const int64_t t = rk > 0 ? rk : 1;
+    // Bracket for the value search: with p_b = min(floor(t*m_b/N), m_b-1) and
+    // q_b = ceil(t*m_b/N) - 1 in every non-empty block b, at least t elements
+    // are <= max_b block_b[p_b] and fewer than t are below min_b block_b[q_b]
+    // (the p_b + 1 and the q_b add up to >= t and < t), so P_k lies between.
+    using U = typename KT<K>::U;
+    U lo0 = 0, hi0 = KT<K>::umax();
+    if constexpr (sizeof(U) <= 8) {
+        __shared__ unsigned long long s_lo, s_hi;
+        if (threadIdx.x == 0) {
+            s_lo = ~0ull;
+            s_hi = 0ull;
+        }
+        __syncthreads();
+        for (int64_t r = threadIdx.x; r < n_B; r += NT) {
+            const int64_t m = b[r] - a[r];
+            if (m <= 0) continue;
+            const unsigned __int128 tm = (unsigned __int128)t * (uint64_t)m;
+            int64_t p = (int64_t)(tm / (uint64_t)N);
+            if (p > m - 1) p = m - 1;
+            const int64_t q = (int64_t)((tm + (uint64_t)N - 1) / (uint64_t)N) - 1;
+            atomicMax(&s_hi, (unsigned long long)KT<K>::to_u(blk.ld(a[r] + p)));
+            atomicMin(&s_lo, (unsigned long long)KT<K>::to_u(blk.ld(a[r] + q)));
+        }
+        __syncthreads();
+        if (s_lo <= s_hi) {
+            lo0 = (U)s_lo;
+            hi0 = (U)s_hi;
+        }
+    }
+    const K v = select_value<NT, K>(blk, a, b, (int)n_B, t, lo0, hi0);
     const int per = (int)((n_B + NT - 1) / NT);
     const int r0 = threadIdx.x * per;
     int64_t lbs = 0, eqs = 0;
