@@ -15,7 +15,7 @@
  * load this file.  It shares no code, header, table or helper with the CUDA
  * library; the product path never calls it.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   R1 block length L = ceil(N/n_B); trailing blocks may be short or empty.
  *   R2 PSRS: sample j (j = 1..n_P-1) of a non-empty sorted block of length m
  *      is block[floor(j*m/n_P)]; empty blocks give no samples; pivot
