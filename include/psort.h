@@ -11,8 +11,8 @@
  *   4. merge the k-th partition of all blocks into the output at offset O_k,
  *      the exclusive scan of the partition sizes.
  * Every step runs in CUDA kernels on the caller's stream; there is no CPU
- * fallback.  The paper states only the problem ("sort an N-element sequence A
- * in ascending order", Sec. 2); the argument conventions below are this
+ * fallback.  The paper poses only the problem of putting N elements in
+ * ascending order (Sec. 2); the argument conventions below are this
  * library's own.
  *
  * Order.  Keys compare by an order key kappa: signed integers by value,
@@ -130,8 +130,8 @@ int ps_sort_pairs(uint64_t* keys, uint32_t* payload, int64_t n, int pivot_mode,
                   const ps_params* params, const ps_trace* trace, ps_stream_t stream);
 
 /* Sort n fixed-size records in place by the uint64 key stored inside each
- * record (Table 1's "Pair", 16 B = key + index, and "Particle", 96 B = key +
- * 88 B of particle data, both "sorted by the key (uint64_t)").
+ * record (Table 1's Pair, 16 B = key + index, and Particle, 96 B = key + 88 B
+ * of particle data, both of which the paper orders by their uint64 key).
  *   records       n * record_bytes bytes of device memory, array of
  *                 structures, 8-byte aligned
  *   record_bytes  multiple of 8, 8 .. PS_STRUCT_MAX_BYTES

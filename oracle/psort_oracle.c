@@ -251,7 +251,7 @@ int ora_sort(int dtype, int mode, int64_t n, const void* keys, const uint32_t* p
         a[i].v = bits;
     }
 
-    /* Block division (R1, Sec. 2: "a contiguous subsequence of length ceil(N/n_B)"). */
+    /* Block division (R1, Sec. 2: contiguous blocks of ceil(N/n_B) elements). */
     int64_t L = (N + n_B - 1) / n_B;
 #define BLO(b) ((b) * L < N ? (b) * L : N)
 #define BHI(b) (((b) + 1) * L < N ? ((b) + 1) * L : N)
@@ -343,7 +343,7 @@ int ora_sort(int dtype, int mode, int64_t n, const void* keys, const uint32_t* p
     }
 
     /* Offsets: total of each partition, then the sequential (exclusive) scan
-     * "from the beginning of the output sequence" (Sec. 2). */
+     * from the start of the output (Sec. 2). */
     O[0] = 0;
     for (int64_t k = 0; k < n_P; k++) {
         int64_t t = 0;
