@@ -969,22 +969,24 @@ __global__ void k_corank(Level L, GBuf<K> src, const Splitter<K>* spl, const int
 }
 
 // Child level completion: hi from the next sibling's lo (or the parent's hi
-// for the last child), output base and size.  One CTA per child.
+// for the last child), output base and size.  One warp per child (NT/32
+// children per CTA), warp-shuffle sums.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* choff, const int* chgrp, Level C)
 {
-    const int64_t c = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
     const int64_t ng = *L.ng < L.cap ? *L.ng : L.cap;
     int64_t nch = choff[ng];
     (void)PS_IN(nch, C.cap + 1, 29);
     if (nch > C.cap) nch = C.cap;
-    if (c >= nch) return;
+    if (c >= nch) return;  // whole warps leave together
     const int Kr = L.K;
     const int64_t g = chgrp[c];
     if (!PS_IN(g, ng, 30) || g < 0 || g >= ng) return;
     const bool last = c + 1 >= choff[g + 1];
     int64_t before = 0, sz = 0;
-    for (int r = threadIdx.x; r < Kr; r += NT) {
+    for (int r = lane; r < Kr; r += 32) {
         const int64_t lo = C.lo[c * Kr + r];
         int64_t hi = last ? L.hi[g * Kr + r] : C.lo[(c + 1) * Kr + r];
         (void)PS_IN(hi - lo, INT64_MAX, 34);  // siblings' windows must not run backwards
@@ -993,9 +995,12 @@ __global__ void __launch_bounds__(NT) k_child_stats(Level L, const int64_t* chof
         before += lo - L.lo[g * Kr + r];
         sz += hi - lo;
     }
-    before = block_sum<NT>(before);
-    sz = block_sum<NT>(sz);
-    if (threadIdx.x == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xFFFFFFFFu, before, o);
+        sz += __shfl_xor_sync(0xFFFFFFFFu, sz, o);
+    }
+    if (lane == 0) {
         C.base[c] = L.base[g] + before;
         C.size[c] = sz;
         if (c == 0) *C.ng = nch;

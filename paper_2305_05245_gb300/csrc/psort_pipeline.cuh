@@ -363,7 +363,7 @@ template <typename K> struct Pipeline {
             }
             {
                 ProfScope ps_(fin ? "children_final" : "children_inblock", s);
-                k_child_stats<128><<<(unsigned)sh.G[l + 1], 128, 0, s>>>(Lv[l], choff, chgrp, Lv[l + 1]);
+                k_child_stats<256><<<(unsigned)((sh.G[l + 1] + 7) / 8), 256, 0, s>>>(Lv[l], choff, chgrp, Lv[l + 1]);
             }
         }
         int64_t* big = (int64_t*)(m + sh.o_big);
