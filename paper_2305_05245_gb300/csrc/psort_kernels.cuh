@@ -213,7 +213,12 @@ template <int W> struct SBuf<Rec, W> {
     }
 };
 
-// ------------------------------------------- asynchronous global->shared copies
+// Shared-memory buffer of a kernel that gives each thread E keys.
+template <typename K, int E> struct TileBuf {
+    using type = SBuf<K, TilePad<K, E>::v>;
+};
+
+// ------------------------------------------- asynchronous global->shared copies// ------------------------------------------- asynchronous global->shared copies
 // cp.async (Ampere-and-later LDGSTS): each thread queues element copies
 // without staging them in registers, so a CTA keeps many loads in flight.
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
@@ -259,6 +264,25 @@ template <typename K, int W = PadOf<K>::v> struct SKeys {
     __device__ __forceinline__ void st(int i, const V& v) const { b.st(i, v); }
     __device__ __forceinline__ static bool lt(const V& x, const V& y) { return key_lt(x, y); }
 };
+template <typename B> struct ViewOf;
+template <typename K, int W> struct ViewOf<SBuf<K, W>> {
+    using type = SKeys<K, W>;
+};
+
+// A thread's E blocked keys from and to shared memory (positions p .. p+E-1).
+template <int E, typename B, typename V>
+__device__ __forceinline__ void load_block(const B& b, int p, V (&r)[E])
+{
+#pragma unroll
+    for (int j = 0; j < E; j++) r[j] = b.ld(p + j);
+}
+template <int E, typename S>
+__device__ __forceinline__ void store_block(const S& s, int p, const typename S::V (&out)[E])
+{
+#pragma unroll
+    for (int i = 0; i < E; i++) s.st(p + i, out[i]);
+}
+
 template <typename K> struct Tagged {
     K key;
     uint64_t tag;
@@ -423,8 +447,7 @@ __device__ void merge_levels_pow2(const S& s)
         V out[E];
         serial_merge<E, false>(s, us + x, um, um + (pos0 - us - x), ue, E, out);
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < E; i++) s.st(pos0 + i, out[i]);
+        store_block<E>(s, pos0, out);
         __syncthreads();
     }
 }
@@ -536,10 +559,7 @@ __device__ void merge_pieces_aligned(const S& s, const int* off, int P, int n)
             serial_merge<E, false>(s, us + x, um, um + (pos0 - us - x), ue, E, out);
         }
         __syncthreads();
-        if (act) {
-#pragma unroll
-            for (int i = 0; i < E; i++) s.st(pos0 + i, out[i]);
-        }
+        if (act) store_block<E>(s, pos0, out);
         __syncthreads();
     }
 }
@@ -593,10 +613,11 @@ template <int NT, int E, typename K, int XF, bool FINAL>
 __global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst in, int64_t n_B, int64_t R0)
 {
     constexpr int T = NT * E;
-    constexpr int W = TilePad<K, E>::v;
+    using SB = typename TileBuf<K, E>::type;
+    using SV = typename ViewOf<SB>::type;
     extern __shared__ __align__(16) char smem[];
     char* sp = smem;
-    SBuf<K, W> sb = SBuf<K, W>::carve(sp, T);
+    SB sb = SB::carve(sp, T);
     const int64_t per_inst = n_B * R0;
     const int64_t inst = blockIdx.x / per_inst;
     const int64_t rest = blockIdx.x - inst * per_inst;
@@ -612,16 +633,26 @@ __global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst
     cp_async_wait_all();
     __syncthreads();
     K r[E];
+    if constexpr (sizeof(K) == 4) {
+        // 4-byte keys: load the whole run, then mask the tail (measured faster)
+        load_block<E>(sb, threadIdx.x * E, r);
 #pragma unroll
-    for (int j = 0; j < E; j++) {
-        const int i = threadIdx.x * E + j;
-        r[j] = i < n ? xform<XF>(sb.ld(i)) : KT<K>::maxkey();
+        for (int j = 0; j < E; j++) {
+            const int i = threadIdx.x * E + j;
+            r[j] = i < n ? xform<XF>(r[j]) : KT<K>::maxkey();
+        }
+    } else {
+        // wider keys: guarded loads keep the register count at 3 CTAs per SM
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int i = threadIdx.x * E + j;
+            r[j] = i < n ? xform<XF>(sb.ld(i)) : KT<K>::maxkey();
+        }
     }
     reg_sort<E>(r);
-#pragma unroll
-    for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
+    store_block<E>(SV{sb}, threadIdx.x * E, r);
     __syncthreads();
-    merge_levels_pow2<NT, E>(SKeys<K, W>{sb});
+    merge_levels_pow2<NT, E>(SV{sb});
     for (int i = threadIdx.x; i < n; i += NT) {
         if (FINAL) dst.template stx<XF>(o + i, sb.ld(i));
         else dst.st(o + i, sb.ld(i));
@@ -1126,11 +1157,12 @@ __global__ void __launch_bounds__(NT, (!BIG && NT <= 256) ? 3 : (!BIG && NT <= 5
     static_assert(!(BIG && ALIGNED), "the oversized-group path merges unpadded pieces");
     static_assert(!(SORTCHUNK && (BIG || ALIGNED)), "copy-and-sort chunks are unpadded and fit the capacity");
     constexpr int CAP = NT * E;
-    constexpr int W = TilePad<K, E>::v;
+    using SB = typename TileBuf<K, E>::type;
+    using SV = typename ViewOf<SB>::type;
     extern __shared__ __align__(16) char smem[];
     const int Kr = C.K;
     char* sp = smem;
-    SBuf<K, W> sb = SBuf<K, W>::carve(sp, CAP);
+    SB sb = SB::carve(sp, CAP);
     int64_t* a = (int64_t*)sp;                       // window starts
     int64_t* b = BIG ? a + Kr : nullptr;             // window ends (BIG only)
     int64_t* x = BIG ? a + 2 * Kr : nullptr;         // sub-chunk ends (BIG only)
@@ -1201,20 +1233,18 @@ __global__ void __launch_bounds__(NT, (!BIG && NT <= 256) ? 3 : (!BIG && NT <= 5
             __syncthreads();
             if constexpr (SORTCHUNK) {
                 K r[E];
+                load_block<E>(sb, threadIdx.x * E, r);
 #pragma unroll
-                for (int j = 0; j < E; j++) {
-                    const int i = threadIdx.x * E + j;
-                    r[j] = i < (int)take ? sb.ld(i) : KT<K>::maxkey();
-                }
+                for (int j = 0; j < E; j++)
+                    if (threadIdx.x * E + j >= (int)take) r[j] = KT<K>::maxkey();
                 reg_sort<E>(r);
-#pragma unroll
-                for (int j = 0; j < E; j++) sb.st(threadIdx.x * E + j, r[j]);
+                store_block<E>(SV{sb}, threadIdx.x * E, r);
                 __syncthreads();
-                merge_levels_pow2<NT, E>(SKeys<K, W>{sb});
+                merge_levels_pow2<NT, E>(SV{sb});
             } else if (ALIGNED) {
-                merge_pieces_aligned<NT, E>(SKeys<K, W>{sb}, off, Kr, (int)tot);
+                merge_pieces_aligned<NT, E>(SV{sb}, off, Kr, (int)tot);
             } else {
-                merge_pieces<NT, E>(SKeys<K, W>{sb}, off, Kr, (int)take);
+                merge_pieces<NT, E>(SV{sb}, off, Kr, (int)take);
             }
             for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
             out += take;

@@ -282,13 +282,13 @@ template <typename K> struct Pipeline {
     static constexpr int BE = ME / 2;  // keys per thread of the oversized-group path
     static size_t merge_smem(int Kr)
     {
-        return SBuf<K, TilePad<K, ME>::v>::bytes(CAP) + 16 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64;
+        return TileBuf<K, ME>::type::bytes(CAP) + 16 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64;
     }
     static size_t big_smem(int Kr)
     {
-        return SBuf<K, TilePad<K, BE>::v>::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64;
+        return TileBuf<K, BE>::type::bytes(MNT * BE) + 32 * (size_t)Kr + 4 * (size_t)(Kr + 1) + 64;
     }
-    static size_t tile_smem() { return SBuf<K, TilePad<K, TE>::v>::bytes(T) + 64; }
+    static size_t tile_smem() { return TileBuf<K, TE>::type::bytes(T) + 64; }
 
     static Inst inst_of(const Plan<K>& pl, const SortArgs& a)
     {
@@ -547,7 +547,7 @@ template <typename K> struct Pipeline {
     {
         if (a.n_max > SNT * SE) return cudaErrorInvalidValue;
         auto f = k_tile_sort<SNT, SE, K, XF, true>;
-        const size_t sm = SBuf<K, TilePad<K, SE>::v>::bytes(SNT * SE) + 64;
+        const size_t sm = TileBuf<K, SE>::type::bytes(SNT * SE) + 64;
         cudaError_t e = smem_attr(f, sm);
         if (e != cudaSuccess) return e;
         Inst in;
