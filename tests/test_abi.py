@@ -127,6 +127,25 @@ def test_injected_allocation_failure_without_gpu(lib):
         assert lib.ps_debug_fail_alloc(0) == 0
 
 
+def test_default_parameter_table_without_gpu(lib):
+    """Automatic parameters: the measured table for 2^14..2^31 keys (one block
+    and one partition up to 2^19), the size heuristic beyond; explicit fields
+    are kept; the allocation-free path is independent of the table."""
+    import paper_2305_05245_gb300 as ps
+    for b in range(14, 20):
+        assert ps.resolve_params(1 << b, 1) == (1, 1)
+        assert ps.resolve_params(1 << b, 0) == (1, 1)
+    assert ps.resolve_params(1 << 30, 1) == (64, 128)
+    assert ps.resolve_params(1 << 30, 3) == (64, 128)   # float64 shares the 64-bit table
+    assert ps.resolve_params(1 << 26, 2) == ps.resolve_params(1 << 26, 0)
+    nb, np_ = ps.resolve_params(1 << 36, 1)             # beyond the table: the heuristic
+    assert nb == 1024 and np_ == 256
+    assert ps.resolve_params(1 << 30, 1, n_blocks=7) == (7, 7)
+    assert ps.resolve_params(1 << 30, 1, n_parts=5)[1] == 5
+    nb, np_ = ps.resolve_params(1 << 30, -1)            # records: heuristic
+    assert 1 <= nb <= 4096 and 1 <= np_ <= 256
+
+
 def test_resolve_and_workspace(lib):
     import paper_2305_05245_gb300 as ps
     nb, np_ = ps.resolve_params(1 << 26, 0)
