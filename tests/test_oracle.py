@@ -125,6 +125,36 @@ def test_float_total_order(ora, dtype, special, mode):
         assert [struct.pack("<d", x) for x in got] == [struct.pack("<d", x) for x in want]
 
 
+def check_float_pivots(ora, lib=None):
+    """Exact-splitting pivots of float keys, bit for bit.  By Eq. 1 (reading:
+    the smallest admissible value) P_k is the element of rank r_k = floor(k N /
+    n_P) of the input in IEEE total order; the reference order comes from
+    Python's float comparison (float_total_key), and pivots are compared as
+    packed bytes so that -0.0 and +0.0, or two NaN-free values with equal
+    magnitude, cannot be confused.  n_P = N makes every element but the last a
+    pivot, so each special value (signed zeros, infinities, denormals, extreme
+    finite values, negatives) is returned as a pivot at least once."""
+    for dtype, special, fmt in (("float32", SPECIAL_F32, "<f"), ("float64", SPECIAL_F64, "<d")):
+        dt = np.float32 if dtype == "float32" else np.float64
+        neg = -np.abs(synth.keys(12, dtype, "gaussian", seed=41))
+        for rep in range(10):
+            perm = synth.splitmix64(rep + 500, 2 * len(special)) % np.uint64(len(special))
+            a = np.concatenate([np.array([special[int(i)] for i in perm], dtype=dt), neg[: rep + 2]])
+            N = len(a)
+            want = insertion_sort(a.tolist(), key=float_total_key)
+            for n_B, n_P in ((1 + rep % 4, N), (2 + rep % 3, 2 + rep % 7)):
+                r = ora.sort(a, 1, n_B, n_P, lib=lib)
+                for k in range(1, n_P):
+                    rk = (k * N) // n_P
+                    pk = want[rk - 1] if rk >= 1 else want[0]
+                    assert struct.pack(fmt, float(r.pivots[k - 1])) == struct.pack(fmt, pk), \
+                        "%s pivot %d of %d: got %r, want %r" % (dtype, k, n_P, float(r.pivots[k - 1]), pk)
+
+
+def test_float_pivots_bit_exact(ora):
+    check_float_pivots(ora)
+
+
 def test_int_extremes(ora):
     a = np.array([2**31 - 1, -2**31, 0, -1, 1, -2**31, 2**31 - 1, 5], dtype=np.int32)
     for mode in (0, 1):

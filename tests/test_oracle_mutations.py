@@ -13,7 +13,7 @@ import pytest
 
 import synth
 from _helpers import float_total_key, insertion_sort, read_golden
-from test_oracle import MODES, _check_partition_invariants
+from test_oracle import MODES, _check_partition_invariants, check_float_pivots
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -35,6 +35,16 @@ MUTANTS = {
     "merge_takes_larger": ("if (less(&lv[b].base[lv[b].pos], &lv[a].base[lv[a].pos])) return b;",
                            "if (less(&lv[a].base[lv[a].pos], &lv[b].base[lv[b].pos])) return b;"),
     "offsets_not_scanned": ("O[k + 1] = O[k] + t;", "O[k + 1] = t;"),
+    # the inverse order key that turns float pivots back into key bits
+    "f32_pivot_branches_swapped": (
+        "if (u & 0x80000000u) return (uint64_t)(u & 0x7fffffffu);\n        return (uint64_t)(uint32_t)~u;",
+        "if (u & 0x80000000u) return (uint64_t)(uint32_t)~u;\n        return (uint64_t)(u & 0x7fffffffu);"),
+    "f64_pivot_branches_swapped": (
+        "if (k & 0x8000000000000000ull) return k & 0x7fffffffffffffffull;\n        return ~k;",
+        "if (k & 0x8000000000000000ull) return ~k;\n        return k & 0x7fffffffffffffffull;"),
+    "f64_pivot_negatives_sign_flip_only": (
+        "if (k & 0x8000000000000000ull) return k & 0x7fffffffffffffffull;\n        return ~k;",
+        "if (k & 0x8000000000000000ull) return k & 0x7fffffffffffffffull;\n        return k ^ 0x8000000000000000ull;"),
 }
 
 
@@ -61,6 +71,7 @@ def _battery(ora, lib):
         a[:3] = [0.0, -0.0, -1.0]
         r = ora.sort(a, mode, 3, 4, lib=lib)
         assert r.out.tolist() == insertion_sort(a.tolist(), key=float_total_key)
+    check_float_pivots(ora, lib)
 
 
 def test_unmutated_passes(ora):
