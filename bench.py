@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -156,18 +157,54 @@ def ncu_traffic(kernel: str, workload: str):
 
 
 # ------------------------------------------------------------ reference arm
+def host_cpu():
+    """nproc and the CPU model of this host (x86 "model name"; on Arm, lscpu's
+    model name, else the implementer/part codes of /proc/cpuinfo)."""
+    model = None
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k and v and k not in fields:
+                    fields[k] = v
+    except OSError:
+        pass
+    model = fields.get("model name")
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if not model and "CPU implementer" in fields:
+        model = "implementer %s part %s" % (fields.get("CPU implementer"), fields.get("CPU part"))
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown"}
+
+
 def oracle_time(a, n_sample: int):
     """Time the CPU oracle (as it stands, one thread) on a bounded sample of
-    the workload; returns (keys per second, seconds, sample size)."""
+    the workload, pinned to one core of this process's allowed set (the
+    first); returns (keys per second, seconds, the core used)."""
     import oracle
     import synth
     oracle.build()
     keys = synth.keys(n_sample, a.dtype, a.dist, seed=synth.seed_for("bench-cpu", a.dtype, a.dist))
     nb = np_ = 64
-    t0 = time.perf_counter()
-    oracle.sort(keys, oracle.EXACT if a.pivot == "exact" else oracle.REGULAR, nb, np_)
-    dt = time.perf_counter() - t0
-    return n_sample / dt, dt
+    allowed = os.sched_getaffinity(0)
+    core = min(allowed)
+    os.sched_setaffinity(0, {core})
+    try:
+        t0 = time.perf_counter()
+        oracle.sort(keys, oracle.EXACT if a.pivot == "exact" else oracle.REGULAR, nb, np_)
+        dt = time.perf_counter() - t0
+    finally:
+        os.sched_setaffinity(0, allowed)
+    return n_sample / dt, dt, core
 
 
 def run_reference(a):
@@ -179,8 +216,9 @@ def run_reference(a):
     for _ in range(a.warmup):
         oracle_time(a, min(n_sample, 1 << 20))
     rates, secs = [], []
+    core = 0
     for _ in range(a.steps):
-        r, dt = oracle_time(a, n_sample)
+        r, dt, core = oracle_time(a, n_sample)
         rates.append(r)
         secs.append(dt)
     value = (n_sample * len(rates)) / sum(secs) / 1e9
@@ -191,9 +229,10 @@ def run_reference(a):
         "vs_baseline": None, "dtype": a.dtype, "data": "synthetic (SplitMix64, seeded)",
         "config": {"workload": workload_name(a), "n": a.n, "dist": a.dist, "pivot": a.pivot,
                    "sample_per_step": n_sample, "n_blocks": 64, "n_parts": 64},
-        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d %s %s keys per step (of the %d-key workload), n_B=n_P=64"
-                                   % (n_sample, a.dtype, a.dist, a.n)},
+        "cpu_baseline": dict({"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                              "sample": "%d %s %s keys per step (of the %d-key workload), n_B=n_P=64, "
+                                        "one thread pinned to core %d"
+                                        % (n_sample, a.dtype, a.dist, a.n, core)}, **host_cpu()),
         "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -734,10 +773,11 @@ def main():
     # the CPU baseline runs first (rank 0, N = 1), before any GPU work
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        rate, dt = oracle_time(a, a.cpu_sample)
-        cpu = {"value": rate / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-               "sample": "%d %s %s keys (of the %d-key workload), n_B=n_P=64, one thread, %.1f s"
-                         % (a.cpu_sample, a.dtype, a.dist, a.n, dt)}
+        rate, dt, core = oracle_time(a, a.cpu_sample)
+        cpu = dict({"value": rate / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                    "sample": "%d %s %s keys (of the %d-key workload), n_B=n_P=64, one thread "
+                              "pinned to core %d, %.1f s" % (a.cpu_sample, a.dtype, a.dist, a.n, core, dt)},
+                   **host_cpu())
 
     import numpy as np
     import torch

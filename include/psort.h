@@ -261,17 +261,21 @@ int ps_server_debug_fail(ps_server* server, int what, int count);
  * that must not allocate device memory: code running while a CUDA graph is
  * being captured by someone else, real-time loops that forbid allocator
  * calls, and hosts whose memory pools are owned and capped by another
- * runtime.  ps_sort_noalloc sorts like ps_sort (same dtypes, pivot modes and
- * automatic parameters, result bit-identical) but takes all of its workspace
- * from one static device array of PS_NOALLOC_SCRATCH_BYTES that the library
- * reserves on every GPU it is loaded on, for the life of the process.
+ * runtime.  ps_sort_noalloc sorts like ps_sort (same dtypes and pivot modes,
+ * result bit-identical) but takes all of its workspace from one static device
+ * array of PS_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU it
+ * is loaded on, for the life of the process.  Its n_B and n_P always come from
+ * the size heuristic (not from tuned or measured table entries, which
+ * ps_sort prefers): the array is sized for the heuristic's shapes, so the
+ * speed may differ from ps_sort's, the result does not.
  *   - n above PS_NOALLOC_MAX_KEYS (or a shape whose workspace would not fit
  *     the array) is rejected with PS_ERR_INVALID_ARG before any work is queued.
  *   - It calls no cudaMalloc, cudaFree or pool allocation.  (Keep profiling
  *     off: ps_profile_enable makes every launch create CUDA events.)
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     outside any stream capture.
+ *   - The first call in each CUDA context (per device: its primary context,
+ *     or a context the caller made current) looks up the array's device
+ *     address there (cudaGetSymbolAddress) and caches it under the context's
+ *     unique ID; make that first call outside any stream capture.
  *   - All calls on a device share the one array and the kernels overwrite
  *     whatever a previous call left there (the counters they need are zeroed
  *     on the stream before use).  Two calls whose work overlaps on the GPU --

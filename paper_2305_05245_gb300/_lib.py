@@ -27,6 +27,7 @@ EXPORTS = ["ps_sort", "ps_sort_ex", "ps_sort_pairs", "ps_sort_host", "ps_resolve
            "ps_batch_plan_create", "ps_batch_run", "ps_batch_plan_destroy", "ps_debug_fail_alloc"]
 
 PS_NOALLOC_MAX_KEYS = 1 << 20
+PS_NOALLOC_SCRATCH_BYTES = 12 << 20
 PS_STRUCT_MAX_BYTES = 4096
 
 

@@ -1,7 +1,9 @@
 """The sort server (ps_server_*): requests of mixed sizes, dtypes and pivot
 modes, submitted from several threads while earlier ones are on the GPU, must
-each come out exactly as ps_sort sorts them alone; admission respects the
-memory budget; close drains everything admitted and queued."""
+each come out exactly as the oracle sorts them (the unique ascending
+permutation, Sec. 2) and exactly as ps_sort sorts them alone on the GPU (the
+same result alone and in the mix); admission respects the memory budget;
+close drains everything admitted and queued."""
 from __future__ import annotations
 
 import threading
@@ -57,6 +59,32 @@ def alone(ps, reqs):
     return out
 
 
+DT_CODE = {"int32": 0, "int64": 1, "float32": 2, "float64": 3}
+
+
+def oracle_results(ora, reqs):
+    """Each request's expected output from the oracle, computed on a host copy
+    of its input: the plain definition for every request, and for the small
+    ones also the four-step oracle run with the (n_B, n_P) the library
+    resolves for that size."""
+    import paper_2305_05245_gb300 as ps
+    out = []
+    for x, mode in reqs:
+        host = x.cpu().numpy()
+        want = ora.reference_sort(host)
+        if 1 < host.size <= (1 << 14):
+            nb, npart = ps.resolve_params(host.size, DT_CODE[str(host.dtype)])
+            r = ora.sort(host, 1 if mode == "exact" else 0, nb, npart)
+            assert r.out.tobytes() == want.tobytes()
+        out.append(want)
+    return out
+
+
+def assert_oracle(work, oracle_want):
+    for i, (w, y) in enumerate(zip(work, oracle_want)):
+        assert w.cpu().numpy().tobytes() == y.tobytes(), "request %d differs from the oracle" % i
+
+
 def wait_all(srv, ids, timeout=120.0):
     got = {}
     t0 = time.time()
@@ -69,9 +97,10 @@ def wait_all(srv, ids, timeout=120.0):
     return got
 
 
-def test_server_mixed_requests_equal_alone(ps):
+def test_server_mixed_requests_equal_alone(ps, ora):
     import torch
     reqs = make_requests(300, 1)
+    owant = oracle_results(ora, reqs)
     want = alone(ps, reqs)
     work = [x.clone() for x, _ in reqs]
     torch.cuda.synchronize()
@@ -82,13 +111,15 @@ def test_server_mixed_requests_equal_alone(ps):
     finally:
         srv.close()
     assert all(got[i] == 0 for i in ids)
+    assert_oracle(work, owant)
     for w, y in zip(work, want):
         assert torch.equal(w, y)
 
 
-def test_server_concurrent_submitters(ps):
+def test_server_concurrent_submitters(ps, ora):
     import torch
     reqs = make_requests(200, 2, max_log=18)
+    owant = oracle_results(ora, reqs)
     want = alone(ps, reqs)
     work = [x.clone() for x, _ in reqs]
     torch.cuda.synchronize()
@@ -109,11 +140,12 @@ def test_server_concurrent_submitters(ps):
     finally:
         srv.close()
     assert sorted(got) == sorted(ids) and all(st == 0 for st in got.values())
+    assert_oracle(work, owant)
     for w, y in zip(work, want):
         assert torch.equal(w, y)
 
 
-def test_server_budget_and_close_drains(ps):
+def test_server_budget_and_close_drains(ps, ora):
     import torch
     from paper_2305_05245_gb300 import PsortError
     srv = ps.Server(budget_bytes=64 << 20, max_inflight=4)
@@ -121,6 +153,7 @@ def test_server_budget_and_close_drains(ps):
     with pytest.raises(PsortError):
         srv.submit(big, "exact")
     reqs = make_requests(40, 3, max_log=16)
+    owant = oracle_results(ora, reqs)
     want = alone(ps, reqs)
     work = [x.clone() for x, _ in reqs]
     torch.cuda.synchronize()
@@ -128,16 +161,18 @@ def test_server_budget_and_close_drains(ps):
         srv.submit(w, mode)
     srv.close()  # waits for every queued and admitted request
     torch.cuda.synchronize()
+    assert_oracle(work, owant)
     for w, y in zip(work, want):
         assert torch.equal(w, y)
 
 
-def test_server_failed_round_does_not_stop_the_others(ps):
+def test_server_failed_round_does_not_stop_the_others(ps, ora):
     """A round that fails at launch (injected on the host) completes its
     requests with an error status, leaves their keys untouched, and the
     server goes on serving correctly."""
     import torch
     reqs = make_requests(40, 5, max_log=18)
+    owant = oracle_results(ora, reqs)
     want = alone(ps, reqs)
     work = [x.clone() for x, _ in reqs]
     torch.cuda.synchronize()
@@ -158,14 +193,16 @@ def test_server_failed_round_does_not_stop_the_others(ps):
             assert torch.equal(w, x), "a failed request's keys changed"
         else:
             assert got[ids[i]] == 0 and torch.equal(w, want[i])
+            assert w.cpu().numpy().tobytes() == owant[i].tobytes()
 
 
-def test_server_survives_failed_streams(ps):
+def test_server_survives_failed_streams(ps, ora):
     """Two of the three stream slots retired (injected): results stay exact on
     the last one.  All three retired: queued and new requests fail with
     PS_ERR_CUDA and close still returns."""
     import torch
     reqs = make_requests(30, 9, max_log=18)
+    owant = oracle_results(ora, reqs)
     want = alone(ps, reqs)
     work = [x.clone() for x, _ in reqs]
     torch.cuda.synchronize()
@@ -175,6 +212,7 @@ def test_server_survives_failed_streams(ps):
         ids = [srv.submit(w, mode) for w, (_, mode) in zip(work, reqs)]
         got = wait_all(srv, ids)
         assert all(got[r] == 0 for r in ids)
+        assert_oracle(work, owant)
         for w, y in zip(work, want):
             assert torch.equal(w, y)
         srv.debug_fail("streams", 1)
