@@ -68,15 +68,28 @@ typedef enum {
     PS_PIVOT_EXACT = 1    /* PSES: exact splitting (Sec. 2.3, Eq. 1, Eq. 2) */
 } ps_pivot_mode;
 
-/* Tuning parameters.  0 in a field means "choose automatically" (the
- * library's size-binned default).  n_blocks = n_B and n_parts = n_P of
- * Sec. 2; both may exceed n (empty blocks or partitions are legal).
- * Limits: 1 <= n_blocks <= 4096, 1 <= n_parts <= 1048576. */
+/* Tuning parameters.  0 in a field means "choose automatically" (a tuned
+ * entry from ps_autotune, else the library's size-binned default).
+ * n_blocks = n_B and n_parts = n_P of Sec. 2; both may exceed n (empty blocks
+ * or partitions are legal).  Limits: 1 <= n_blocks <= 4096,
+ * 1 <= n_parts <= 1048576.
+ * items_per_thread and block_threads fix the launch shape of the two data
+ * passes of the GPU design, the tile sort of step 1 and the chunk merges of
+ * the in-block passes and of step 4: every CTA holds block_threads *
+ * items_per_thread keys in shared memory (the tile and the chunk capacity).
+ * They are an implementation choice, not part of the paper's method, and do
+ * not change the result.  Supported: items_per_thread in {16, 32} and
+ * block_threads in {128, 256, 512} for keys-only sorts (a 0 in one of the
+ * two fields takes 32 items or 256 threads); records (ps_sort_pairs,
+ * ps_sort_struct) take only the automatic shape (0, 0) or (16, 256).  Any
+ * other value is PS_ERR_INVALID_ARG; a shape not offered for the dtype is
+ * PS_ERR_UNSUPPORTED.  Batched sorts and the server use the automatic shape. */
 typedef struct {
     int64_t n_blocks;
     int64_t n_parts;
-    int64_t merge_variant; /* step 4 (Sec. 2.2), one of ps_merge_variant */
-    int64_t reserved;      /* must be 0 */
+    int64_t merge_variant;    /* step 4 (Sec. 2.2), one of ps_merge_variant */
+    int32_t items_per_thread; /* 0 = automatic, 16 or 32 */
+    int32_t block_threads;    /* 0 = automatic, 128, 256 or 512 */
 } ps_params;
 
 /* How step 4 merges the pieces of one chunk of a partition (Sec. 2.2 and the
@@ -192,17 +205,21 @@ int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode,
  * in a process-wide table that automatic parameters then use for sorts of
  * round(log2 n) = b.  batched = 0 tunes single sorts; batched = 1 tunes the
  * size bins of ps_sort_batch (batches of about 2^26 keys in segments of
- * (2^(b-1), 2^b] keys) and fills a separate table.  Keys per thread and
- * threads per CTA are compile-time constants and are not tuned.  Allocates
+ * (2^(b-1), 2^b] keys) and fills a separate table.  Single sorts then also
+ * time every launch shape (items_per_thread x block_threads) the dtype offers
+ * at the fastest (n_B, n_P) and record the fastest shape with them; batched
+ * bins keep the automatic shape.  Allocates
  * 2 * max(n_max, 2^26) keys of workspace; waits for `stream` (each candidate
  * is timed with CUDA events: one untimed run, median of three).  n_max at
  * most 2^34. */
 int ps_autotune(int dtype, int pivot_mode, int64_t n_min, int64_t n_max, int batched, ps_stream_t stream);
 
 /* Read (PS_ERR_NOT_FOUND when untuned) or write one entry of the tuned table:
- * out/p->n_blocks and n_parts for sorts of round(log2 n) = log2_n keys of
- * dtype's width.  ps_autotune_set with p NULL (or both fields 0) clears the
- * entry; it lets a caller restore a table saved from an earlier run. */
+ * out/p->n_blocks, n_parts, items_per_thread and block_threads for sorts of
+ * round(log2 n) = log2_n keys of dtype's width (a shape of 0, 0 = the
+ * automatic one).  ps_autotune_set with p NULL (or n_blocks and n_parts 0)
+ * clears the entry; it lets a caller restore a table saved from an earlier
+ * run. */
 int ps_autotune_get(int dtype, int batched, int log2_n, ps_params* out);
 int ps_autotune_set(int dtype, int batched, int log2_n, const ps_params* p);
 

@@ -55,13 +55,16 @@ def _mode(m) -> int:
 _MERGES = {"tree": 0, "sort": 1, "select": 2, 0: 0, 1: 1, 2: 2}
 
 
-def _params(n_blocks: int, n_parts: int, merge_variant="tree"):
+def _params(n_blocks: int, n_parts: int, merge_variant="tree", items_per_thread: int = 0,
+            block_threads: int = 0):
     p = _lib.PsParams()
     p.n_blocks = n_blocks
     p.n_parts = n_parts
     if merge_variant not in _MERGES:
         raise ValueError("merge_variant must be 'tree', 'sort' or 'select'")
     p.merge_variant = _MERGES[merge_variant]
+    p.items_per_thread = items_per_thread
+    p.block_threads = block_threads
     return p
 
 
@@ -123,12 +126,14 @@ def _make_trace(n: int, code: int, n_blocks: int, n_parts: int, key_dtype, devic
 
 
 def sort(keys, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, trace: bool = False,
-         stream=None, merge_variant="tree"):
+         stream=None, merge_variant="tree", items_per_thread: int = 0, block_threads: int = 0):
     """Sort a contiguous 1-D CUDA tensor in place (int32, int64, float32,
     float64, uint32, uint64).  Returns a Trace when ``trace`` is true.
     ``merge_variant`` picks step 4's chunk merge: "tree" (pairwise merge
     levels, the default), "sort" (copy the pieces and sort) or "select"
-    (one selection tree per chunk); all give the same result."""
+    (one selection tree per chunk); all give the same result.
+    ``items_per_thread`` (16, 32) and ``block_threads`` (128, 256, 512) fix
+    the launch shape of the data passes (0 = automatic)."""
     lib = _lib.load()
     if not keys.is_cuda or keys.dim() != 1 or not keys.is_contiguous():
         raise ValueError("keys must be a contiguous 1-D CUDA tensor")
@@ -138,7 +143,8 @@ def sort(keys, pivot_mode="exact", n_blocks: int = 0, n_parts: int = 0, trace: b
     if trace:
         tr, ct = _make_trace(n, code, n_blocks, n_parts, keys.dtype, keys.device, False)
     rc = lib.ps_sort_ex(keys.data_ptr() if n else None, n, code, _mode(pivot_mode),
-                        ctypes.byref(_params(n_blocks, n_parts, merge_variant)),
+                        ctypes.byref(_params(n_blocks, n_parts, merge_variant, items_per_thread,
+                                             block_threads)),
                         ctypes.byref(ct) if ct is not None else None, _stream_handle(stream))
     _lib.check(lib, "ps_sort_ex", rc)
     return tr
@@ -200,7 +206,8 @@ def autotune(dtype, pivot_mode="exact", n_min: int = 1 << 14, n_max: int = 1 << 
              stream=None) -> dict:
     """Run the library's autotuner (ps_autotune) for keys of ``dtype``'s width
     over the power-of-two sizes in [n_min, n_max]; returns the tuned table
-    {log2 n: (n_blocks, n_parts)} that automatic parameters now use."""
+    {log2 n: (n_blocks, n_parts, items_per_thread, block_threads)} that
+    automatic parameters now use (a shape of 0, 0 is the automatic one)."""
     lib = _lib.load()
     code = _code_of(dtype)
     rc = lib.ps_autotune(code, _mode(pivot_mode), n_min, n_max, 1 if batched else 0, _stream_handle(stream))
@@ -209,22 +216,25 @@ def autotune(dtype, pivot_mode="exact", n_min: int = 1 << 14, n_max: int = 1 << 
 
 
 def autotune_table(dtype, batched: bool = False) -> dict:
-    """The tuned entries {log2 n: (n_blocks, n_parts)} for ``dtype``'s width."""
+    """The tuned entries {log2 n: (n_blocks, n_parts, items_per_thread,
+    block_threads)} for ``dtype``'s width."""
     lib = _lib.load()
     code = _code_of(dtype)
     out = {}
     for b in range(64):
         p = _lib.PsParams()
         if lib.ps_autotune_get(code, 1 if batched else 0, b, ctypes.byref(p)) == 0:
-            out[b] = (p.n_blocks, p.n_parts)
+            out[b] = (p.n_blocks, p.n_parts, p.items_per_thread, p.block_threads)
     return out
 
 
-def autotune_set(dtype, log2_n: int, n_blocks: int, n_parts: int, batched: bool = False) -> None:
+def autotune_set(dtype, log2_n: int, n_blocks: int, n_parts: int, batched: bool = False,
+                 items_per_thread: int = 0, block_threads: int = 0) -> None:
     """Write (or, with zeros, clear) one tuned entry, e.g. to restore a saved table."""
     lib = _lib.load()
     p = _lib.PsParams()
     p.n_blocks, p.n_parts = n_blocks, n_parts
+    p.items_per_thread, p.block_threads = items_per_thread, block_threads
     _lib.check(lib, "ps_autotune_set", lib.ps_autotune_set(_code_of(dtype), 1 if batched else 0, log2_n,
                                                             ctypes.byref(p)))
 

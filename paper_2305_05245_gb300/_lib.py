@@ -33,7 +33,8 @@ PS_STRUCT_MAX_BYTES = 4096
 
 class PsParams(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int64), ("n_parts", ctypes.c_int64),
-                ("merge_variant", ctypes.c_int64), ("reserved", ctypes.c_int64)]
+                ("merge_variant", ctypes.c_int64), ("items_per_thread", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32)]
 
 
 class PsTrace(ctypes.Structure):

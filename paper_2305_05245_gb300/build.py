@@ -17,7 +17,21 @@ LIB_CHECKED = os.path.join(HERE, "libpsort_checked.so")
 BUILD = os.path.join(HERE, "_build")
 
 SOURCES = ["psort_u32.cu", "psort_u64.cu", "psort_rec.cu", "psort_api.cu", "psort_noalloc.cu",
-           "psort_server.cu", "psort_struct.cu"]
+           "psort_server.cu", "psort_struct.cu", "psort_shapes.cu"]
+# Launch shapes (key bits, items per thread, threads per CTA) compiled besides
+# the automatic one, each from psort_shape.cu into an object of its own; the
+# 64-bit (32, 256) shape is the automatic one and is not repeated.
+SHAPES = [(b, e, t) for b in (32, 64) for e in (16, 32) for t in (128, 256, 512)
+          if (b, e, t) != (64, 32, 256)]
+
+
+def units():
+    """(source, object name, extra flags) of every translation unit."""
+    out = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
+    for b, e, t in SHAPES:
+        out.append(("psort_shape.cu", "psort_shape_u%d_e%d_t%d.o" % (b, e, t),
+                    ["-DPS_SHAPE_BITS=%d" % b, "-DPS_SHAPE_ITEMS=%d" % e, "-DPS_SHAPE_THREADS=%d" % t]))
+    return out
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -48,18 +62,20 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     cc = nvcc()
     extra = ["-DPS_CHECKED"] if checked else []
 
-    def compile_one(src):
-        obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, name, flags = unit
+        obj = os.path.join(bdir, name)
+        cmd = [cc, *ARCH, *FLAGS, *extra, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
+            raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (name, r.stdout, r.stderr))
         if verbose:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    todo = units()
+    with cf.ThreadPoolExecutor(max_workers=min(len(todo), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(compile_one, todo))
     tmp = lib + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

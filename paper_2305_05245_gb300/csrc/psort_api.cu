@@ -143,10 +143,11 @@ static int64_t pow2_floor(int64_t x)
 //
 // Autotuned parameters (ps_autotune) take precedence over these defaults for
 // automatic fields: g_tune[context][family][round(log2 n)] holds (n_B, n_P)
+// and the launch shape (items per thread, threads per CTA; 0, 0 = automatic)
 // measured fastest for sorts of about n keys, context 0 for single sorts and
 // 1 for the size bins of batched sorts; family 0 = 32-bit keys, 1 = 64-bit.
 struct TuneEntry {
-    int32_t nb, np;
+    int32_t nb, np, items, threads;
 };
 static std::mutex g_tune_mu;
 static TuneEntry g_tune[2][2][64];
@@ -167,7 +168,8 @@ static int tune_bin(int64_t n)
     return b;
 }
 
-static bool tuned(int ctx, int dtype, int64_t n, int32_t* nb, int32_t* np)
+static bool tuned(int ctx, int dtype, int64_t n, int32_t* nb, int32_t* np, int32_t* items = nullptr,
+                  int32_t* threads = nullptr)
 {
     const int f = tune_family(dtype);
     if (f < 0 || n < 2) return false;
@@ -176,6 +178,8 @@ static bool tuned(int ctx, int dtype, int64_t n, int32_t* nb, int32_t* np)
     if (e.nb <= 0) return false;
     *nb = e.nb;
     *np = e.np;
+    if (items) *items = e.items;
+    if (threads) *threads = e.threads;
     return true;
 }
 
@@ -229,15 +233,27 @@ static bool measured_default(int ctx, int dtype, int64_t n, int32_t* nb, int32_t
 }
 
 // Automatic fields: a tuned entry for this size (context ctx) when there is
-// one, else the measured default, else the heuristic.  Explicit fields are kept.
+// one, else the measured default, else the heuristic.  Explicit fields are
+// kept.  A tuned entry supplies its launch shape too when n_blocks and both
+// shape fields are automatic; otherwise (0, 0) stays the family's automatic
+// shape.
 static void resolve(int64_t n, int dtype, const ps_params* in, ps_params* out, int ctx = 0)
 {
     ps_params r;
     memset(&r, 0, sizeof(r));
     if (in) r = *in;
-    int32_t nb = 0, np = 0;
-    if ((r.n_blocks <= 0 || r.n_parts <= 0) &&
-        (tuned(ctx, dtype, n, &nb, &np) || measured_default(ctx, dtype, n, &nb, &np))) {
+    int32_t nb = 0, np = 0, it = 0, th = 0;
+    const bool auto_shape = r.items_per_thread == 0 && r.block_threads == 0;
+    if ((r.n_blocks <= 0 || r.n_parts <= 0) && tuned(ctx, dtype, n, &nb, &np, &it, &th)) {
+        if (r.n_blocks <= 0) {
+            r.n_blocks = nb;
+            if (r.n_parts <= 0) r.n_parts = np;
+            if (auto_shape) {
+                r.items_per_thread = it;
+                r.block_threads = th;
+            }
+        }
+    } else if ((r.n_blocks <= 0 || r.n_parts <= 0) && measured_default(ctx, dtype, n, &nb, &np)) {
         if (r.n_blocks <= 0) {
             r.n_blocks = nb;
             if (r.n_parts <= 0) r.n_parts = np;
@@ -252,8 +268,29 @@ static int check_params(const ps_params* p)
     if (p->n_blocks < 0 || p->n_blocks > MAX_BLOCKS) return PS_ERR_INVALID_ARG;
     if (p->n_parts < 0 || p->n_parts > MAX_PARTS) return PS_ERR_INVALID_ARG;
     if (p->merge_variant < PS_MERGE_TREE || p->merge_variant > PS_MERGE_SELECT) return PS_ERR_INVALID_ARG;
-    if (p->reserved != 0) return PS_ERR_INVALID_ARG;
+    if (p->items_per_thread != 0 && p->items_per_thread != 16 && p->items_per_thread != 32) return PS_ERR_INVALID_ARG;
+    if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 && p->block_threads != 512)
+        return PS_ERR_INVALID_ARG;
     return PS_OK;
+}
+
+// The launch shape a sort runs with: nullptr for the family's automatic
+// shape, else the compiled shape; PS_ERR_UNSUPPORTED in *rc when the shape is
+// not offered for the dtype.
+static const ShapeEntry* shape_of(int dtype, int items, int threads, int* rc)
+{
+    *rc = PS_OK;
+    if (items == 0 && threads == 0) return nullptr;
+    const int it = items ? items : 32, th = threads ? threads : 256;
+    if (dtype == -1) {
+        if (it != 16 || th != 256) *rc = PS_ERR_UNSUPPORTED;
+        return nullptr;
+    }
+    const int bits = (dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32) ? 32 : 64;
+    if (bits == 64 && it == 32 && th == 256) return nullptr;  // the automatic 64-bit shape
+    const ShapeEntry* e = find_shape(bits, it, th);
+    if (!e) *rc = PS_ERR_UNSUPPORTED;
+    return e;
 }
 
 // PS_LOG=1 in the environment: one line per sort on stderr with the
@@ -270,9 +307,13 @@ static int log_level()
 static int dispatch(SortArgs& a)
 {
     if (log_level() >= 1)
-        fprintf(stderr, "psort: n=%lld dtype=%d mode=%d n_B=%lld n_P=%lld instances=%lld merge_variant=%d\n",
+        fprintf(stderr, "psort: n=%lld dtype=%d mode=%d n_B=%lld n_P=%lld instances=%lld merge_variant=%d shape=%dx%d\n",
                 (long long)a.n, a.dtype, a.mode, (long long)a.n_B, (long long)a.n_P, (long long)a.n_inst,
-                a.merge_variant);
+                a.merge_variant, a.items, a.threads);
+    int rc = PS_OK;
+    const ShapeEntry* sh = shape_of(a.dtype, a.items, a.threads, &rc);
+    if (rc != PS_OK) return rc;
+    if (sh) return sh->run(a);
     switch (a.dtype) {
     case PS_I32: case PS_F32: case PS_U32: return run_sort_u32(a);
     case PS_I64: case PS_F64: case PS_U64: return run_sort_u64(a);
@@ -304,6 +345,8 @@ static int sort_common(void* keys, uint32_t* payload, int64_t n, int dtype, int 
     a.n_B = r.n_blocks;
     a.n_P = r.n_parts;
     a.merge_variant = (int)r.merge_variant;
+    a.items = r.items_per_thread;
+    a.threads = r.block_threads;
     a.trace = trace;
     a.stream = (cudaStream_t)stream;
     return dispatch(a);
@@ -604,9 +647,29 @@ static int autotune(int dtype, int mode, int64_t n_min, int64_t n_max, int batch
                 bnp = cand.second;
             }
         }
+        // single sorts: every launch shape of the family at the fastest
+        // (n_B, n_P); the automatic shape (0, 0) is the one timed above
+        int32_t bit = 0, bth = 0;
+        for (const ShapeEntry* const* sh = all_shapes(); !batched && rc == PS_OK && bnb > 0 && *sh; sh++) {
+            if ((*sh)->bits != (f == 0 ? 32 : 64)) continue;
+            ps_params p;
+            memset(&p, 0, sizeof(p));
+            p.n_blocks = bnb;
+            p.n_parts = bnp;
+            p.items_per_thread = (*sh)->items;
+            p.block_threads = (*sh)->threads;
+            auto run = [&]() { return sort_common(keys, nullptr, n, dtype, mode, &p, nullptr, s); };
+            float ms = 0.f;
+            rc = time_median(run, restore, s, 3, &ms);
+            if (rc == PS_OK && ms < best) {
+                best = ms;
+                bit = (*sh)->items;
+                bth = (*sh)->threads;
+            }
+        }
         if (rc == PS_OK && bnb > 0) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tune[batched ? 1 : 0][f][b] = TuneEntry{(int32_t)bnb, (int32_t)bnp};
+            g_tune[batched ? 1 : 0][f][b] = TuneEntry{(int32_t)bnb, (int32_t)bnp, bit, bth};
         }
     }
     ws_free(buf, s);
@@ -767,6 +830,8 @@ int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode, const ps
         a.n_B = r.n_blocks;
         a.n_P = r.n_parts;
         a.merge_variant = (int)r.merge_variant;
+        a.items = r.items_per_thread;
+        a.threads = r.block_threads;
         a.trace = nullptr;
         a.stream = s;
         a.src_keys = mapped;
@@ -809,6 +874,22 @@ int ps_workspace_bytes(int64_t n, int dtype, const ps_params* params, size_t* ou
     }
     ps_params r;
     resolve(n, dtype, params, &r);
+    const ShapeEntry* sh = shape_of(dtype, r.items_per_thread, r.block_threads, &rc);
+    if (rc != PS_OK) return rc;
+    if (sh) {
+        SortArgs a;
+        a.keys = nullptr;
+        a.payload = nullptr;
+        a.n = n;
+        a.dtype = dtype;
+        a.mode = PS_PIVOT_REGULAR;
+        a.n_B = r.n_blocks;
+        a.n_P = r.n_parts;
+        a.trace = nullptr;
+        a.stream = nullptr;
+        *out = sh->ws(a);
+        return PS_OK;
+    }
     switch (dtype) {
     case PS_I32: case PS_F32: case PS_U32: *out = ws_bytes_u32(n, r.n_blocks, r.n_parts); break;
     case -1: *out = ws_bytes_rec(n, r.n_blocks, r.n_parts); break;
@@ -837,6 +918,8 @@ int ps_autotune_get(int dtype, int batched, int log2_n, ps_params* out)
     memset(out, 0, sizeof(*out));
     out->n_blocks = e.nb;
     out->n_parts = e.np;
+    out->items_per_thread = e.items;
+    out->block_threads = e.threads;
     return PS_OK;
 }
 
@@ -845,11 +928,15 @@ int ps_autotune_set(int dtype, int batched, int log2_n, const ps_params* p)
     const int f = tune_family(dtype);
     if (f < 0) return PS_ERR_UNSUPPORTED;
     if (log2_n < 0 || log2_n > 63 || (batched != 0 && batched != 1)) return PS_ERR_INVALID_ARG;
-    TuneEntry t{0, 0};
+    TuneEntry t{0, 0, 0, 0};
     if (p && (p->n_blocks != 0 || p->n_parts != 0)) {
         if (p->n_blocks < 1 || p->n_blocks > MAX_BLOCKS || p->n_parts < 1 || p->n_parts > MAX_PARTS)
             return PS_ERR_INVALID_ARG;
-        t = TuneEntry{(int32_t)p->n_blocks, (int32_t)p->n_parts};
+        if (check_params(p) != PS_OK) return PS_ERR_INVALID_ARG;
+        int rc = PS_OK;
+        shape_of(f == 0 ? PS_U32 : PS_U64, p->items_per_thread, p->block_threads, &rc);
+        if (rc != PS_OK) return rc;
+        t = TuneEntry{(int32_t)p->n_blocks, (int32_t)p->n_parts, p->items_per_thread, p->block_threads};
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[batched][f][log2_n] = t;

@@ -21,6 +21,9 @@ struct SortArgs {
     int mode;            // ps_pivot_mode
     int64_t n_B, n_P;    // resolved
     int merge_variant = 0;  // ps_merge_variant of step 4
+    // Launch shape of the data passes (ps_params items_per_thread and
+    // block_threads); 0, 0 = the family's automatic shape.
+    int items = 0, threads = 0;
     const ps_trace* trace;
     cudaStream_t stream;
     // Batched sorts: n_inst independent instances sharing n_B and n_P, with
@@ -96,5 +99,19 @@ constexpr int64_t SMALL_SEG = 1024;
 // Workspace bytes of the sort a describes (batched instances included).
 size_t ws_bytes_args_u32(const SortArgs& a);
 size_t ws_bytes_args_u64(const SortArgs& a);
+
+// Keys-only pipelines compiled for other launch shapes than the automatic one
+// (one translation unit per shape: psort_shape.cu built with -D flags).
+struct ShapeEntry {
+    int bits;     // key width: 32 or 64
+    int items;    // keys per thread of the tile sort and the chunk merge
+    int threads;  // threads per CTA of both
+    int (*run)(const SortArgs&);
+    size_t (*ws)(const SortArgs&);
+};
+// The entry for (bits, items, threads), or nullptr if none was compiled.
+const ShapeEntry* find_shape(int bits, int items, int threads);
+// Every compiled shape (for the autotuner), terminated by a null entry.
+const ShapeEntry* const* all_shapes();
 
 }  // namespace ps

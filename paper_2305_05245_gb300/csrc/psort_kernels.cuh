@@ -394,6 +394,60 @@ template <int E, typename K> __device__ __forceinline__ void reg_sort(K (&r)[E])
     OddEvenSort<0, E>::run(r);
 }
 
+// ------------------------------------------------ warp-shuffle merge levels
+// Exchange of a key with the lane whose index differs by the bits of m.
+__device__ __forceinline__ uint32_t shfl_key(uint32_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
+__device__ __forceinline__ uint64_t shfl_key(uint64_t v, int m)
+{
+    const uint32_t lo = __shfl_xor_sync(0xFFFFFFFFu, (uint32_t)v, m);
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, (uint32_t)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+// The lower lane of a compare pair keeps the smaller key, the upper lane the
+// larger one (equal keys are identical bit patterns, so either may stay).
+template <typename K> __device__ __forceinline__ K keep(const K& mine, const K& other, bool upper)
+{
+    return (key_lt(other, mine) != upper) ? other : mine;
+}
+// Each lane holds a sorted run of E keys (blocked: lane l holds positions
+// l*E .. l*E+E-1 of its warp's 32*E keys).  LEV bitonic merge levels double
+// the sorted runs LEV times without shared memory (Batcher's bitonic merge,
+// Knuth TAOCP vol. 3, 5.3.4, ex. 10): at level s, units of U = 2^(s+1)
+// lanes hold two sorted runs; the first stage compares position i of the
+// unit with position 2m-1-i (m = half the unit: lanes l and l^(U-1), registers
+// j and E-1-j) and leaves two bitonic halves, every key of the lower one no
+// larger than any of the upper one; half-cleaners at lane distances U/4 .. 1
+// (shuffles) and register distances E/2 .. 1 (in-thread) then sort each
+// half.  Every index is a compile-time constant or a lane bit.
+template <int E, int LEV, typename K>
+__device__ __forceinline__ void warp_merge_levels(K (&r)[E])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 0; s < LEV; s++) {
+        const int U = 2 << s;
+        const bool hi_run = (lane & (U >> 1)) != 0;
+#pragma unroll
+        for (int j = 0; j < E / 2; j++) {
+            const K pa = shfl_key(r[E - 1 - j], U - 1);  // partner's E-1-j faces my j
+            const K pb = shfl_key(r[j], U - 1);          // partner's j faces my E-1-j
+            r[j] = keep(r[j], pa, hi_run);
+            r[E - 1 - j] = keep(r[E - 1 - j], pb, hi_run);
+        }
+#pragma unroll
+        for (int d = U >> 2; d >= 1; d >>= 1) {
+            const bool up = (lane & d) != 0;
+#pragma unroll
+            for (int j = 0; j < E; j++) r[j] = keep(r[j], shfl_key(r[j], d), up);
+        }
+#pragma unroll
+        for (int d = E / 2; d >= 1; d >>= 1)
+#pragma unroll
+            for (int j = 0; j < E; j++)
+                if ((j & d) == 0) cas(r[j], r[j + d]);
+    }
+}
+
 // -------------------------------------------- shared-memory multiway merge
 // Serial merge of E outputs from the heads A[ai..aend) and B[bi..bend) of one
 // merge unit (stable: A wins ties).  Reads one element past an exhausted
@@ -436,12 +490,12 @@ __device__ __forceinline__ int merge_path(const S& s, int us, int um, int ue, in
 // U = 2, 4, ... pieces' worth, all powers of two); every thread owns exactly E
 // outputs that never straddle a unit.
 template <int NT, int E, typename S>
-__device__ void merge_levels_pow2(const S& s)
+__device__ void merge_levels_pow2(const S& s, int U0 = 2 * E)
 {
     using V = typename S::V;
     const int pos0 = threadIdx.x * E;
 #pragma unroll 1
-    for (int U = 2 * E; U <= NT * E; U <<= 1) {
+    for (int U = U0; U <= NT * E; U <<= 1) {
         const int us = pos0 & ~(U - 1), um = us + U / 2, ue = us + U;
         const int x = merge_path(s, us, um, ue, pos0 - us);
         V out[E];
@@ -602,17 +656,81 @@ __device__ __forceinline__ void block_bounds(int64_t N, int64_t n_B, int64_t b, 
     be = bs + L < N ? bs + L : N;
 }
 
+// CTAs per SM a data-pass kernel of NT threads with E keys per thread is
+// compiled for: as many as the register file holds at about 16 + w*E
+// registers a thread (w = 32-bit words a key takes in registers), and no
+// more than 1024 threads per SM in all.
+template <typename K, int NT, int E> constexpr int data_ctas()
+{
+    constexpr int w = sizeof(K) == 4 ? 1 : sizeof(K) == 8 ? 2 : 3;
+    constexpr int c = 65536 / (NT * (16 + w * E));
+    constexpr int cap = 1024 / NT < 1 ? 1 : 1024 / NT;
+    return c < 1 ? 1 : (c > cap ? cap : c);
+}
+
 // ------------------------------------------------------------ step 1: tiles
+// Loads of one tile straight into registers, for plain keys: warp w takes
+// tile positions [w*32*E, (w+1)*32*E) and lane l the 16-byte vectors at
+// positions w*32*E + v*32*VEC + l*VEC (VEC keys each), so that every warp-wide
+// load covers 32*16 contiguous bytes.  Which keys a lane holds does not
+// matter (they are sorted next), so no shared-memory staging is needed.
+// A full tile whose start is 16-byte aligned takes vector loads; a short or
+// unaligned one takes guarded scalar loads at the same positions.  Missing
+// keys of a short tile become the largest key.
+template <int NT, int E, typename K, int XF>
+__device__ __forceinline__ void tile_load_regs(const GBuf<K>& src, int64_t o, int n, K (&r)[E])
+{
+    constexpr int VEC = 16 / (int)sizeof(K);
+    static_assert(E % VEC == 0, "keys per thread must be a multiple of the vector width");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = w * 32 * E + lane * VEC;
+    const K* g = src.p + o;
+    if (n == NT * E && ((uintptr_t)g & 15) == 0) {
+#pragma unroll
+        for (int v = 0; v < E / VEC; v++) {
+            const int i = base + v * 32 * VEC;
+            if constexpr (sizeof(K) == 8) {
+                ulonglong2 x = make_ulonglong2(0, 0);
+                if (PS_IN(o + i + 1, src.n, 3)) x = __ldcs((const ulonglong2*)(g + i));
+                r[v * 2] = xform<XF>((K)x.x);
+                r[v * 2 + 1] = xform<XF>((K)x.y);
+            } else {
+                uint4 x = make_uint4(0, 0, 0, 0);
+                if (PS_IN(o + i + 3, src.n, 3)) x = __ldcs((const uint4*)(g + i));
+                r[v * 4] = xform<XF>((K)x.x);
+                r[v * 4 + 1] = xform<XF>((K)x.y);
+                r[v * 4 + 2] = xform<XF>((K)x.z);
+                r[v * 4 + 3] = xform<XF>((K)x.w);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < E / VEC; v++)
+#pragma unroll
+            for (int q = 0; q < VEC; q++) {
+                const int i = base + v * 32 * VEC + q;
+                r[v * VEC + q] = i < n ? xform<XF>(src.ld(o + i)) : KT<K>::maxkey();
+            }
+    }
+}
+
 // One CTA sorts one tile of NT*E keys of one block of one instance (tiles
 // never straddle a block boundary; every block gets R0 tile slots, the
 // number the longest block needs).  Loads apply the order-key transform XF.
 // Missing keys of a short tile count as the largest key, which sorts last
 // and is never written.  FINAL: the tile is the whole sorted result, so the
-// store applies the inverse transform.
-template <int NT, int E, typename K, int XF, bool FINAL>
-__global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst in, int64_t n_B, int64_t R0)
+// store applies the inverse transform.  Plain keys: loads straight into
+// registers (tile_load_regs), a register sorting network per thread, WLEV
+// warp-shuffle merge levels, then shared-memory merge-path levels for the
+// rest.  Records: cp.async staging through shared memory, then the same
+// network and shared-memory levels.
+template <int NT, int E, typename K, int XF, bool FINAL, int WLEV = 0>
+__global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
+    k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst in, int64_t n_B, int64_t R0)
 {
     constexpr int T = NT * E;
+    constexpr bool PLAIN = sizeof(K) == 4 || sizeof(K) == 8;
+    static_assert(PLAIN || WLEV == 0, "records take no shuffle levels");
     using SB = typename TileBuf<K, E>::type;
     using SV = typename ViewOf<SB>::type;
     extern __shared__ __align__(16) char smem[];
@@ -629,30 +747,25 @@ __global__ void __launch_bounds__(NT) k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst
     if (ts >= be) return;
     const int64_t o = in.off(inst) + ts;
     const int n = (int)(be - ts < T ? be - ts : T);
-    for (int i = threadIdx.x; i < n; i += NT) cp_elem(sb, i, src, o + i);
-    cp_async_wait_all();
-    __syncthreads();
     K r[E];
-    if constexpr (sizeof(K) == 4) {
-        // 4-byte keys: load the whole run, then mask the tail (measured faster)
-        load_block<E>(sb, threadIdx.x * E, r);
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-            const int i = threadIdx.x * E + j;
-            r[j] = i < n ? xform<XF>(r[j]) : KT<K>::maxkey();
-        }
+    if constexpr (PLAIN) {
+        tile_load_regs<NT, E, K, XF>(src, o, n, r);
     } else {
-        // wider keys: guarded loads keep the register count at 3 CTAs per SM
+        for (int i = threadIdx.x; i < n; i += NT) cp_elem(sb, i, src, o + i);
+        cp_async_wait_all();
+        __syncthreads();
 #pragma unroll
         for (int j = 0; j < E; j++) {
             const int i = threadIdx.x * E + j;
             r[j] = i < n ? xform<XF>(sb.ld(i)) : KT<K>::maxkey();
         }
+        __syncthreads();
     }
     reg_sort<E>(r);
+    if constexpr (WLEV > 0) warp_merge_levels<E, WLEV>(r);
     store_block<E>(SV{sb}, threadIdx.x * E, r);
     __syncthreads();
-    merge_levels_pow2<NT, E>(SV{sb});
+    merge_levels_pow2<NT, E>(SV{sb}, E << (WLEV + 1));
     for (int i = threadIdx.x; i < n; i += NT) {
         if (FINAL) dst.template stx<XF>(o + i, sb.ld(i));
         else dst.st(o + i, sb.ld(i));
@@ -803,7 +916,7 @@ template <typename K> struct Splitter {
 
 // Per group: cut every run into blocks of S elements (the last block of a run
 // may be shorter) and take each block's last element as a sample standing for
-// the block's keys; S is chosen so that the pool holds about J*max(2K, 96)
+// the block's keys; S is chosen so that the pool holds about J*max(SPC*K, 96)
 // samples (at most POOL).
 // The pool is sorted in shared memory (a multiway merge of the per-run sample
 // lists, stable, so ties order by run then position).  Splitter j (1..J-1) is
@@ -814,7 +927,7 @@ template <typename K> struct Splitter {
 // [c*S, min(c*S + S - 1, len_r)] (all samples: exactly len_r).  These windows
 // go to the child level's lo/hi tables, where k_corank narrows them to the
 // exact co-rank with a search over at most S elements.
-template <int NT, int E, typename K>
+template <int NT, int E, typename K, int SPC>
 __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t* choff, int* chgrp,
                                              Splitter<K>* spl, int64_t ccap, Level C)
 {
@@ -852,10 +965,10 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
     int* jpos = mpos + POOL;              // pool position of splitter j (-1: none)
     int* off = jpos + (POOL / 2 + 1);
     const int64_t M = L.size[g];
-    // about max(2K, 96) samples per child: enough to place every splitter
+    // about max(SPC*K, 96) samples per child: enough to place every splitter
     // within a few percent of its target rank (each run's co-rank is known
     // to within its S-key block), and no more than the pool holds
-    int64_t ptarget = J * (2 * (int64_t)Kr > 96 ? 2 * (int64_t)Kr : 96);
+    int64_t ptarget = J * (SPC * (int64_t)Kr > 96 ? SPC * (int64_t)Kr : 96);
     if (ptarget > POOL) ptarget = POOL;
     const int64_t room = ptarget - Kr > 1 ? ptarget - Kr : 1;
     const int64_t S = M <= room ? 1 : (M + room - 1) / room;
@@ -1151,7 +1264,7 @@ __device__ void exact_corank(const GBuf<K>& src, const int64_t* a, const int64_t
 // is sorted as a whole, ignoring that the pieces are sorted (the "copy and
 // sort" way of multiway merging, Sec. 2.2).
 template <int NT, int E, typename K, int XF, bool BIG, bool ALIGNED, bool SORTCHUNK = false>
-__global__ void __launch_bounds__(NT, (!BIG && NT <= 256) ? 3 : (!BIG && NT <= 512) ? 2 : 1) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
+__global__ void __launch_bounds__(NT, (BIG ? 1 : data_ctas<K, NT, E>())) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
                                               unsigned long long* nbig)
 {
     static_assert(!(BIG && ALIGNED), "the oversized-group path merges unpadded pieces");

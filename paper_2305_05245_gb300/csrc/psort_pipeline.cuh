@@ -12,18 +12,37 @@
 
 namespace ps {
 
-// Threads per CTA and keys per thread of the tile sort (TNT, TE), of the
-// chunk merge (MNT, ME; MNT*ME is the chunk capacity) and of the sample pool
-// (PNT, PE; PNT*PE samples).
+// Threads per CTA and keys per thread of the tile sort (TNT, TE), warp-shuffle
+// merge levels of the tile sort (TW), of the chunk merge (MNT, ME; MNT*ME is
+// the chunk capacity) and of the sample pool (PNT, PE; PNT*PE samples).
+// Shuffle levels measured on GB300 (2^30 keys): 64-bit keys 2 (a shuffle
+// level's compare-exchanges cost more ALU work than a shared-memory level
+// beyond that), 32-bit keys 5 (all levels inside a warp).
+#ifndef PS_TILE_WLEV32
+#define PS_TILE_WLEV32 5
+#endif
+#ifndef PS_TILE_WLEV64
+#define PS_TILE_WLEV64 2
+#endif
+// Target chunk size of a merge, in percent of the room a chunk has after the
+// average padding (splitters land within a few percent of their targets;
+// oversized chunks take the exact sub-chunk path).
+#ifndef PS_MERGE_FILL
+#define PS_MERGE_FILL 90
+#endif
+// Sample-pool samples per child, as a multiple of the fan-in (at least 96).
+#ifndef PS_POOL_SPC
+#define PS_POOL_SPC 2
+#endif
 template <typename K> struct Cfg;
 template <> struct Cfg<uint32_t> {
-    static constexpr int TNT = 256, TE = 32, MNT = 512, ME = 32, PNT = 1024, PE = 8;
+    static constexpr int TNT = 256, TE = 32, TW = PS_TILE_WLEV32, MNT = 512, ME = 32, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<uint64_t> {
-    static constexpr int TNT = 256, TE = 32, MNT = 256, ME = 32, PNT = 1024, PE = 8;
+    static constexpr int TNT = 256, TE = 32, TW = PS_TILE_WLEV64, MNT = 256, ME = 32, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<Rec> {
-    static constexpr int TNT = 256, TE = 16, MNT = 256, ME = 16, PNT = 512, PE = 8;
+    static constexpr int TNT = 256, TE = 16, TW = 0, MNT = 256, ME = 16, PNT = 512, PE = 8;
 };
 
 constexpr int64_t FMAX = 256;  // largest fan-in of one in-block merge pass
@@ -52,10 +71,10 @@ struct MergeShape {
 };
 
 // Everything the launches need to know about one sort's shape.
-template <typename K> struct Plan {
-    static constexpr int T = Cfg<K>::TNT * Cfg<K>::TE;    // tile
-    static constexpr int CAP = Cfg<K>::MNT * Cfg<K>::ME;  // merge chunk capacity
-    static constexpr int POOL = Cfg<K>::PNT * Cfg<K>::PE;
+template <typename K, typename CF = Cfg<K>> struct Plan {
+    static constexpr int T = CF::TNT * CF::TE;    // tile
+    static constexpr int CAP = CF::MNT * CF::ME;  // merge chunk capacity
+    static constexpr int POOL = CF::PNT * CF::PE;
     int64_t N;      // extent of the key arrays
     int64_t n_inst; // instances (1 for a single sort)
     int64_t Nmax;   // longest instance
@@ -72,21 +91,21 @@ template <typename K> struct Plan {
     // Chunks of a fan-in K merge are merged with their pieces padded to
     // multiples of ME (aligned merge) while K*(ME-1), the worst-case padding,
     // stays within a quarter of the capacity.
-    static bool aligned(int64_t K_) { return K_ * (Cfg<K>::ME - 1) * 4 <= CAP; }
+    static bool aligned(int64_t K_) { return K_ * (CF::ME - 1) * 4 <= CAP; }
     // chunks aim at 85% of the capacity left after the average padding
     // (splitters land within about 10% of their targets); oversized ones take
     // the slow exact path
     static int64_t cnom(int64_t K_)
     {
-        const int64_t room = aligned(K_) ? CAP - K_ * (Cfg<K>::ME - 1) / 2 : CAP;
-        return room * 85 / 100;
+        const int64_t room = aligned(K_) ? CAP - K_ * (CF::ME - 1) / 2 : CAP;
+        return room * PS_MERGE_FILL / 100;
     }
     static int64_t jcap(int64_t K_) { return std::max<int64_t>(1, (POOL / 2 - K_) / 2); }
-    // children per refinement level: the pool takes about max(2K, 96) samples
-    // per child, so J is capped near POOL/max(2K, 96)
+    // children per refinement level: the pool takes about max(SPC*K, 96)
+    // samples per child, so J is capped near POOL/max(SPC*K, 96)
     static int64_t jlevel(int64_t K_)
     {
-        int64_t ji = POOL / std::max<int64_t>(2 * K_, 96);
+        int64_t ji = POOL / std::max<int64_t>(PS_POOL_SPC * K_, 96);
         ji = std::min<int64_t>(64, std::max<int64_t>(2, ji));
         return std::min(ji, jcap(K_));
     }
@@ -152,15 +171,15 @@ template <typename K> struct Plan {
         size_t mbytes = 0;
         int64_t R = R0, W = T;
         for (int p = 0; p < npass; p++) {
-            int rem = npass - p;
-            int64_t f = 2;  // smallest fan-in with f^rem >= R
-            while (true) {
-                long double q = 1;
-                for (int i = 0; i < rem; i++) q *= (long double)f;
-                if (q >= (long double)R || f >= FMAX) break;
-                f++;
-            }
-            F[p] = std::min<int64_t>(f, R);
+            // A pass of fan-in F merges its chunks in ceil(log2 F) shared-memory
+            // levels, so fan-ins are powers of two that share the ceil(log2 R)
+            // levels still needed evenly (larger first): 2048 runs take 64 x 32
+            // (11 levels) rather than 46 x 45 (12 levels).
+            const int rem = npass - p;
+            int lvl = 0;
+            while ((int64_t(1) << lvl) < R) lvl++;
+            const int lp = (lvl + rem - 1) / rem;
+            F[p] = std::min<int64_t>(std::min<int64_t>(int64_t(1) << lp, FMAX), R);
             const int64_t Rp = (L + W - 1) / W;
             const int64_t gpb = (Rp + F[p] - 1) / F[p];
             inblock[p] = shape((int)F[p], n_inst * n_B * gpb, std::min<int64_t>(F[p] * W, L));
@@ -270,8 +289,18 @@ static inline int xf_of(int dtype)
     }
 }
 
-template <typename K> struct Pipeline {
-    using C = Cfg<K>;
+// The caller's pivot buffers of a trace, viewed as a key buffer.
+template <typename K> static GBuf<K> trace_gbuf(const ps_trace* t);
+template <> inline GBuf<uint32_t> trace_gbuf<uint32_t>(const ps_trace* t) { return GBuf<uint32_t>{(uint32_t*)t->pivots, INT64_MAX}; }
+template <> inline GBuf<uint64_t> trace_gbuf<uint64_t>(const ps_trace* t) { return GBuf<uint64_t>{(uint64_t*)t->pivots, INT64_MAX}; }
+template <> inline GBuf<Rec> trace_gbuf<Rec>(const ps_trace* t)
+{
+    return GBuf<Rec>{(uint64_t*)t->pivots, t->pivot_payload, INT64_MAX};
+}
+
+template <typename K, typename CF = Cfg<K>> struct Pipeline {
+    using C = CF;
+    using PlanK = Plan<K, CF>;
     static constexpr int TNT = C::TNT, TE = C::TE, MNT = C::MNT, ME = C::ME, PNT = C::PNT, PE = C::PE;
     static constexpr int T = TNT * TE, CAP = MNT * ME, POOL = PNT * PE;
 
@@ -290,7 +319,7 @@ template <typename K> struct Pipeline {
     }
     static size_t tile_smem() { return TileBuf<K, TE>::type::bytes(T) + 64; }
 
-    static Inst inst_of(const Plan<K>& pl, const SortArgs& a)
+    static Inst inst_of(const PlanK& pl, const SortArgs& a)
     {
         Inst in;
         in.base = a.inst_base;
@@ -301,11 +330,12 @@ template <typename K> struct Pipeline {
     }
 
     template <int XF>
-    static cudaError_t tile_sort(GBuf<K> src, GBuf<K> dst, const Plan<K>& pl, const SortArgs& a_, cudaStream_t s)
+    static cudaError_t tile_sort(GBuf<K> src, GBuf<K> dst, const PlanK& pl, const SortArgs& a_, cudaStream_t s)
     {
         // the tile sort is the whole sort when there is one block, one
         // partition and no in-block pass
-        auto f = (pl.direct && pl.npass == 0) ? k_tile_sort<TNT, TE, K, XF, true> : k_tile_sort<TNT, TE, K, XF, false>;
+        auto f = (pl.direct && pl.npass == 0) ? k_tile_sort<TNT, TE, K, XF, true, C::TW>
+                                              : k_tile_sort<TNT, TE, K, XF, false, C::TW>;
         cudaError_t e = smem_attr(f, tile_smem());
         if (e != cudaSuccess) return e;
         const int64_t grid = pl.n_inst * pl.n_B * pl.R0;
@@ -320,7 +350,7 @@ template <typename K> struct Pipeline {
     // variant: ps_merge_variant of the last level's chunk merge.
     template <int XF>
     static cudaError_t merge(const MergeJob& job, const MergeShape& sh, GBuf<K> src, GBuf<K> dst,
-                             const Plan<K>& pl, char* ws, cudaStream_t s, int variant = PS_MERGE_TREE)
+                             const PlanK& pl, char* ws, cudaStream_t s, int variant = PS_MERGE_TREE)
     {
         const bool fin = job.kind == 1;
         char* m = ws + pl.o_merge;
@@ -341,7 +371,7 @@ template <typename K> struct Pipeline {
             const int64_t nt = sh.G[0] * Kr;
             k_root_windows<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(job, sh.G[0], Lv[0]);
         }
-        auto fp = k_pool<PNT, PE, K>;
+        auto fp = k_pool<PNT, PE, K, PS_POOL_SPC>;
         if ((e = smem_attr(fp, pool_smem(Kr))) != cudaSuccess) return e;
         for (int l = 0; l < sh.nlev; l++) {
             int64_t* choff = (int64_t*)(m + sh.o_choff[l]);
@@ -384,7 +414,7 @@ template <typename K> struct Pipeline {
             return cudaGetLastError();
         }
         auto fm = variant == PS_MERGE_SORT ? k_merge<MNT, ME, K, XF, false, false, true>
-                  : Plan<K>::aligned(Kr)   ? k_merge<MNT, ME, K, XF, false, true>
+                  : PlanK::aligned(Kr)   ? k_merge<MNT, ME, K, XF, false, true>
                                            : k_merge<MNT, ME, K, XF, false, false>;
         if ((e = smem_attr(fm, merge_smem(Kr))) != cudaSuccess) return e;
         {
@@ -401,7 +431,7 @@ template <typename K> struct Pipeline {
         return cudaGetLastError();
     }
 
-    template <int XF> static cudaError_t run_xf(const SortArgs& a, const Plan<K>& pl, char* ws)
+    template <int XF> static cudaError_t run_xf(const SortArgs& a, const PlanK& pl, char* ws)
     {
         cudaStream_t s = a.stream;
         GBuf<K> user = gbuf_user<K>(a);
@@ -520,9 +550,9 @@ template <typename K> struct Pipeline {
         return cudaGetLastError();
     }
 
-    static GBuf<K> trace_buf(const ps_trace* t);
+    static GBuf<K> trace_buf(const ps_trace* t) { return trace_gbuf<K>(t); }
 
-    static void make_plan(Plan<K>& pl, const SortArgs& a)
+    static void make_plan(PlanK& pl, const SortArgs& a)
     {
         if (a.inst_base)
             pl.make(a.extent, a.n_inst, a.n_max, a.n_sum, a.n_B, a.n_P, a.mode);
@@ -546,7 +576,7 @@ template <typename K> struct Pipeline {
     template <int XF> static cudaError_t small_xf(const SortArgs& a)
     {
         if (a.n_max > SNT * SE) return cudaErrorInvalidValue;
-        auto f = k_tile_sort<SNT, SE, K, XF, true>;
+        auto f = k_tile_sort<SNT, SE, K, XF, true, C::TW>;
         const size_t sm = TileBuf<K, SE>::type::bytes(SNT * SE) + 64;
         cudaError_t e = smem_attr(f, sm);
         if (e != cudaSuccess) return e;
@@ -563,7 +593,7 @@ template <typename K> struct Pipeline {
 
     static int run(const SortArgs& a)
     {
-        Plan<K> pl;
+        PlanK pl;
         make_plan(pl, a);
         char* ws = nullptr;
         int rc = ws_alloc((void**)&ws, pl.total, a.stream);
@@ -583,7 +613,7 @@ template <typename K> struct Pipeline {
     // allocates nothing.  PS_ERR_INVALID_ARG if the plan does not fit.
     static int run_on(const SortArgs& a, char* ws, size_t cap)
     {
-        Plan<K> pl;
+        PlanK pl;
         make_plan(pl, a);
         if (pl.total > cap) return PS_ERR_INVALID_ARG;
         cudaError_t e;
@@ -599,24 +629,17 @@ template <typename K> struct Pipeline {
     // Workspace of one (possibly multi-instance) sort as described by a.
     static size_t ws_bytes_for(const SortArgs& a)
     {
-        Plan<K> pl;
+        PlanK pl;
         make_plan(pl, a);
         return pl.total;
     }
 
     static size_t ws_bytes(int64_t n, int64_t nb, int64_t np)
     {
-        Plan<K> pl;
+        PlanK pl;
         pl.make(n, 1, n, n, nb, np, PS_PIVOT_REGULAR);
         return pl.total;
     }
 };
-
-template <> inline GBuf<uint32_t> Pipeline<uint32_t>::trace_buf(const ps_trace* t) { return GBuf<uint32_t>{(uint32_t*)t->pivots, INT64_MAX}; }
-template <> inline GBuf<uint64_t> Pipeline<uint64_t>::trace_buf(const ps_trace* t) { return GBuf<uint64_t>{(uint64_t*)t->pivots, INT64_MAX}; }
-template <> inline GBuf<Rec> Pipeline<Rec>::trace_buf(const ps_trace* t)
-{
-    return GBuf<Rec>{(uint64_t*)t->pivots, t->pivot_payload, INT64_MAX};
-}
 
 }  // namespace ps

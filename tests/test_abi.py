@@ -51,9 +51,17 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
     p.n_blocks, p.n_parts = 4, (1 << 20) + 1
     assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
-    p.n_parts, p.reserved = 4, 1
-    assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
-    p.reserved, p.merge_variant = 0, 3
+    p.n_parts = 4
+    # launch shapes: unknown values are invalid, unoffered combinations unsupported
+    for it, th in [(8, 256), (24, 0), (0, 64), (32, 1024), (-16, 256)]:
+        p.items_per_thread, p.block_threads = it, th
+        assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1, (it, th)
+    for it, th in [(32, 512), (32, 0), (0, 128)]:
+        p.items_per_thread, p.block_threads = it, th
+        assert lib.ps_sort_pairs(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 10, 0,
+                                 ctypes.byref(p), None, None) == -2, (it, th)
+    p.items_per_thread, p.block_threads = 0, 0
+    p.merge_variant = 3
     assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
     p.merge_variant = -1
     assert lib.ps_sort_ex(None, 10, 0, 1, ctypes.byref(p), None, None) == -1
@@ -106,6 +114,18 @@ def test_autotune_table_without_gpu(lib):
     r2.n_blocks = 64
     assert lib.ps_resolve_params(1 << 40, 0, ctypes.byref(r2), ctypes.byref(r)) == 0
     assert r.n_blocks == 64  # explicit fields win
+    # an entry carries a launch shape too; it applies when n_blocks and the
+    # shape are automatic, and unoffered or invalid shapes are refused
+    p.items_per_thread, p.block_threads = 16, 512
+    assert lib.ps_autotune_set(0, 0, 40, ctypes.byref(p)) == 0
+    assert lib.ps_autotune_get(0, 0, 40, ctypes.byref(q)) == 0
+    assert (q.n_blocks, q.n_parts, q.items_per_thread, q.block_threads) == (48, 96, 16, 512)
+    assert lib.ps_resolve_params(1 << 40, 0, None, ctypes.byref(r)) == 0
+    assert (r.items_per_thread, r.block_threads) == (16, 512)
+    assert lib.ps_resolve_params(1 << 40, 0, ctypes.byref(r2), ctypes.byref(r)) == 0
+    assert (r.items_per_thread, r.block_threads) == (0, 0)  # explicit n_B: automatic shape
+    p.items_per_thread, p.block_threads = 24, 512
+    assert lib.ps_autotune_set(0, 0, 40, ctypes.byref(p)) == -1
     assert lib.ps_autotune_set(0, 0, 40, None) == 0
     assert lib.ps_autotune_get(0, 0, 40, ctypes.byref(q)) == -7
 

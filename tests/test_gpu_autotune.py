@@ -29,10 +29,11 @@ def test_autotune_single(ps, ora):
     try:
         table = ps.autotune("int32", "exact", 1 << 16, 1 << 18)
         assert sorted(table) == [16, 17, 18]
-        for b, (nb, np_) in table.items():
+        for b, (nb, np_, it, th) in table.items():
             assert 1 <= nb <= 4096 and 1 <= np_ <= 1024
+            assert (it, th) == (0, 0) or (it in (16, 32) and th in (128, 256, 512))
         n = (1 << 17) + 123
-        assert ps.resolve_params(n, 0) == table[17]
+        assert ps.resolve_params(n, 0) == table[17][:2]
         x = synth.keys_torch(n, "int32", "uniform", seed=synth.seed_for("tune-single"))
         want = ora.reference_sort(x.cpu().numpy())
         ps.sort(x, "exact")
