@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=32.0, help="serve: admission budget")
+    ap.add_argument("--serial-fraction", type=float, default=0.25,
+                    help="serve: leading fraction of the trace replayed through serial per-request ps_sort")
     ap.add_argument("--segments", type=int, default=20000)
     ap.add_argument("--baseline-segments", type=int, default=2000,
                     help="segments timed with one ps_sort call each (batch workload)")
@@ -717,7 +719,7 @@ def run_serve(a):
     lat, span, bad = serve_once(trace)
     keys = sum(r[1] for r in trace)
     # serial plain path: one ps_sort per request, in arrival order, each waited for
-    nb = min(len(trace), max(50, len(trace) // 4))
+    nb = min(len(trace), max(50, int(len(trace) * a.serial_fraction)))
     base_lat = []
     t0 = time.perf_counter()
     for req in trace[:nb]:
@@ -743,7 +745,8 @@ def run_serve(a):
                    "requests": len(trace), "keys": keys},
         "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": 1e3 * lat[-1]},
         "failed_requests": bad,
-        "serial_per_request_ps_sort": {"requests": nb, "keys_per_s": base_keys / base_span,
+        "serial_per_request_ps_sort": {"requests": nb, "trace_fraction": nb / max(1, len(trace)),
+                                       "keys_per_s": base_keys / base_span,
                                        "latency_ms": {"p50": pct(base_lat, 0.5), "p99": pct(base_lat, 0.99)}},
     }
     print(json.dumps(line))

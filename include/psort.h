@@ -83,7 +83,9 @@ typedef enum {
  * two fields takes 32 items or 256 threads); records (ps_sort_pairs,
  * ps_sort_struct) take only the automatic shape (0, 0) or (16, 256).  Any
  * other value is PS_ERR_INVALID_ARG; a shape not offered for the dtype is
- * PS_ERR_UNSUPPORTED.  Batched sorts and the server use the automatic shape. */
+ * PS_ERR_UNSUPPORTED.  Batched sorts (and the server's rounds, which are
+ * batched sorts) take, per size bin, the shape of the bin's entry in the
+ * batched autotune table, else the automatic one. */
 typedef struct {
     int64_t n_blocks;
     int64_t n_parts;
@@ -205,10 +207,10 @@ int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode,
  * in a process-wide table that automatic parameters then use for sorts of
  * round(log2 n) = b.  batched = 0 tunes single sorts; batched = 1 tunes the
  * size bins of ps_sort_batch (batches of about 2^26 keys in segments of
- * (2^(b-1), 2^b] keys) and fills a separate table.  Single sorts then also
- * time every launch shape (items_per_thread x block_threads) the dtype offers
- * at the fastest (n_B, n_P) and record the fastest shape with them; batched
- * bins keep the automatic shape.  Allocates
+ * (2^(b-1), 2^b] keys) and fills a separate table.  Each size then also
+ * times every launch shape (items_per_thread x block_threads) the dtype
+ * offers at the fastest (n_B, n_P) and records the fastest shape with them
+ * (for batches: per size bin).  Allocates
  * 2 * max(n_max, 2^26) keys of workspace; waits for `stream` (each candidate
  * is timed with CUDA events: one untimed run, median of three).  n_max at
  * most 2^34. */

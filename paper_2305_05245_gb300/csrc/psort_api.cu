@@ -381,6 +381,7 @@ struct BatchBin {
     size_t at;                // offset of the bin's starts in the instance table
     int64_t cnt, nmax, nsum;  // instances, longest, total keys
     int64_t n_B, n_P;
+    int items, threads;       // launch shape (0, 0: automatic)
     bool small;               // at most SMALL_SEG keys each: one small CTA per segment
 };
 struct BatchPlan {
@@ -439,6 +440,8 @@ static int batch_make_plan(const std::vector<int64_t>& off, int dtype, int mode,
         }
         bb.n_B = r.n_blocks;
         bb.n_P = r.n_parts;
+        bb.items = b <= 1 ? 0 : r.items_per_thread;
+        bb.threads = b <= 1 ? 0 : r.block_threads;
         bb.small = b == 0;
         bp->bins.push_back(bb);
     }
@@ -456,6 +459,8 @@ static SortArgs batch_bin_args(const BatchPlan& bp, const BatchBin& bb, const in
     a.mode = bp.mode;
     a.n_B = bb.n_B;
     a.n_P = bb.n_P;
+    a.items = bb.items;
+    a.threads = bb.threads;
     a.trace = nullptr;
     a.stream = s;
     a.inst_base = dev_table + bb.at;
@@ -479,9 +484,15 @@ static int batch_launch(const BatchPlan& bp, const int64_t* dev_table, void* key
     int rc = PS_OK;
     for (size_t i = 0; i < bp.bins.size() && rc == PS_OK; i++) {
         SortArgs a = batch_bin_args(bp, bp.bins[i], dev_table, keys, s);
-        if (bp.bins[i].small) rc = narrow ? run_small_u32(a) : run_small_u64(a);
-        else if (ws) rc = narrow ? run_sort_u32_on(a, ws, cap) : run_sort_u64_on(a, ws, cap);
-        else rc = dispatch(a);
+        if (bp.bins[i].small) {
+            rc = narrow ? run_small_u32(a) : run_small_u64(a);
+        } else if (ws) {
+            const ShapeEntry* sh = shape_of(a.dtype, a.items, a.threads, &rc);
+            if (rc == PS_OK)
+                rc = sh ? sh->run_on(a, ws, cap) : narrow ? run_sort_u32_on(a, ws, cap) : run_sort_u64_on(a, ws, cap);
+        } else {
+            rc = dispatch(a);
+        }
     }
     return rc;
 }
@@ -647,10 +658,10 @@ static int autotune(int dtype, int mode, int64_t n_min, int64_t n_max, int batch
                 bnp = cand.second;
             }
         }
-        // single sorts: every launch shape of the family at the fastest
-        // (n_B, n_P); the automatic shape (0, 0) is the one timed above
+        // every launch shape of the family at the fastest (n_B, n_P); the
+        // automatic shape (0, 0) is the one timed above
         int32_t bit = 0, bth = 0;
-        for (const ShapeEntry* const* sh = all_shapes(); !batched && rc == PS_OK && bnb > 0 && *sh; sh++) {
+        for (const ShapeEntry* const* sh = all_shapes(); rc == PS_OK && bnb > 0 && *sh; sh++) {
             if ((*sh)->bits != (f == 0 ? 32 : 64)) continue;
             ps_params p;
             memset(&p, 0, sizeof(p));
@@ -658,7 +669,10 @@ static int autotune(int dtype, int mode, int64_t n_min, int64_t n_max, int batch
             p.n_parts = bnp;
             p.items_per_thread = (*sh)->items;
             p.block_threads = (*sh)->threads;
-            auto run = [&]() { return sort_common(keys, nullptr, n, dtype, mode, &p, nullptr, s); };
+            auto run = [&]() {
+                if (batched) return batch_sort(off, keys, dtype, mode, s, nullptr, 0, &p);
+                return sort_common(keys, nullptr, n, dtype, mode, &p, nullptr, s);
+            };
             float ms = 0.f;
             rc = time_median(run, restore, s, 3, &ms);
             if (rc == PS_OK && ms < best) {
@@ -755,7 +769,10 @@ int ps_batch_plan_create(const int64_t* host_seg_offsets, int64_t n_segs, int dt
     for (const BatchBin& bb : p->plan.bins) {
         if (bb.small) continue;
         SortArgs a = batch_bin_args(p->plan, bb, nullptr, nullptr, nullptr);
-        ws = std::max(ws, narrow_dtype(dtype) ? ws_bytes_args_u32(a) : ws_bytes_args_u64(a));
+        int src = PS_OK;
+        const ShapeEntry* sh = shape_of(dtype, a.items, a.threads, &src);
+        if (src != PS_OK && rc == PS_OK) rc = src;
+        ws = std::max(ws, sh ? sh->ws(a) : narrow_dtype(dtype) ? ws_bytes_args_u32(a) : ws_bytes_args_u64(a));
     }
     cudaError_t e = cudaSuccess;
     if (rc == PS_OK && !p->plan.table.empty()) {

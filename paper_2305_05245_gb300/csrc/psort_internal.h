@@ -108,6 +108,7 @@ struct ShapeEntry {
     int threads;  // threads per CTA of both
     int (*run)(const SortArgs&);
     size_t (*ws)(const SortArgs&);
+    int (*run_on)(const SortArgs&, char* ws, size_t cap);  // on a caller's workspace
 };
 // The entry for (bits, items, threads), or nullptr if none was compiled.
 const ShapeEntry* find_shape(int bits, int items, int threads);

@@ -28,8 +28,10 @@ using KeyT = std::conditional_t<PS_SHAPE_BITS == 32, uint32_t, uint64_t>;
 using Pipe = Pipeline<KeyT, ShapeCfg<KeyT, PS_SHAPE_ITEMS, PS_SHAPE_THREADS>>;
 int run_shape(const SortArgs& a) { return Pipe::run(a); }
 size_t ws_shape(const SortArgs& a) { return Pipe::ws_bytes_for(a); }
+int run_shape_on(const SortArgs& a, char* ws, size_t cap) { return Pipe::run_on(a, ws, cap); }
 }  // namespace
 
-extern const ShapeEntry PS_SHAPE_NAME = {PS_SHAPE_BITS, PS_SHAPE_ITEMS, PS_SHAPE_THREADS, &run_shape, &ws_shape};
+extern const ShapeEntry PS_SHAPE_NAME = {PS_SHAPE_BITS, PS_SHAPE_ITEMS, PS_SHAPE_THREADS, &run_shape, &ws_shape,
+                                         &run_shape_on};
 
 }  // namespace ps

@@ -168,3 +168,35 @@ def test_batch_plan_run_and_cuda_graph(ps, ora, dtype):
             assert x.cpu().numpy().tobytes() == reference(ora, fresh, offs).tobytes()
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("dtype,items,threads", [("int32", 16, 512), ("int64", 32, 512), ("float64", 16, 128)])
+def test_batch_bins_with_tuned_launch_shapes(ps, ora, dtype, items, threads):
+    """Batched size bins whose tuned entries carry a launch shape run with it,
+    through ps_sort_batch and through a batch plan (whose workspace is sized
+    for that shape), and every segment still equals the oracle's result."""
+    import torch
+    bins = range(14, 21)
+    try:
+        for b in bins:
+            ps.autotune_set(dtype, b, 4, 4, batched=True, items_per_thread=items, block_threads=threads)
+        assert all(ps.autotune_table(dtype, batched=True)[b][2:] == (items, threads) for b in bins)
+        keys, offs = make_batch(300, 19, dtype, "uniform", seed=synth.seed_for("batch-shape", dtype) % 100000,
+                                special=SPECIAL)
+        want = reference(ora, keys, offs).tobytes()
+        x = to_dev(keys)
+        ps.sort_batch(x, torch.from_numpy(offs).cuda(), "exact")
+        torch.cuda.synchronize()
+        assert x.cpu().numpy().tobytes() == want
+        plan = ps.BatchPlan(offs, getattr(torch, dtype), "regular")
+        try:
+            x = to_dev(keys)
+            plan.run(x)
+            torch.cuda.synchronize()
+            assert x.cpu().numpy().tobytes() == want
+        finally:
+            plan.close()
+    finally:
+        for b in bins:
+            ps.autotune_set(dtype, b, 0, 0, batched=True)
+    assert ps.autotune_table(dtype, batched=True) == {}
