@@ -30,9 +30,13 @@ namespace ps {
 #ifndef PS_MERGE_FILL
 #define PS_MERGE_FILL 90
 #endif
-// Sample-pool samples per child, as a multiple of the fan-in (at least 96).
+// Sample-pool samples per child, as a multiple of the fan-in (at least 96),
+// and the most children one refinement level makes.
 #ifndef PS_POOL_SPC
 #define PS_POOL_SPC 2
+#endif
+#ifndef PS_POOL_JMAX
+#define PS_POOL_JMAX 64
 #endif
 template <typename K> struct Cfg;
 template <> struct Cfg<uint32_t> {
@@ -106,7 +110,7 @@ template <typename K, typename CF = Cfg<K>> struct Plan {
     static int64_t jlevel(int64_t K_)
     {
         int64_t ji = POOL / std::max<int64_t>(PS_POOL_SPC * K_, 96);
-        ji = std::min<int64_t>(64, std::max<int64_t>(2, ji));
+        ji = std::min<int64_t>(PS_POOL_JMAX, std::max<int64_t>(2, ji));
         return std::min(ji, jcap(K_));
     }
 
