@@ -690,6 +690,100 @@ static int autotune(int dtype, int mode, int64_t n_min, int64_t n_max, int batch
     return rc;
 }
 
+// ps_sort_host on page-locked host keys the device can address, for sorts
+// of several blocks: the blocks of step 1 are independent, so the host keys
+// travel to the device in groups of blocks on a copy stream while the blocks
+// that have arrived are sorted (one batched block sort per group: every block
+// an instance with one block and one partition, its result kept as order
+// keys).  Steps 2 to 4 then run on the sorted blocks and the final merge
+// writes the result straight into the host buffer.  The host link (about
+// 0.2 TB/s each way on GB300) is the bound; this hides the block sort's
+// merge passes behind the transfer instead of running them after it.
+static constexpr int64_t HOST_PIPE_MIN = int64_t(1) << 24;
+
+static int host_pipelined(const void* host_keys, void* mapped, void* d, int64_t n, int dtype, int mode,
+                          const ps_params& r, cudaStream_t s)
+{
+    const int64_t nb = r.n_blocks, L = (n + nb - 1) / nb;
+    const size_t kb = dtype_size(dtype);
+    // instance table of the blocks: all starts, then all lengths
+    std::vector<int64_t> tab(2 * (size_t)nb);
+    for (int64_t b = 0; b < nb; b++) {
+        const int64_t bs = std::min(b * L, n), be = std::min(bs + L, n);
+        tab[(size_t)b] = bs;
+        tab[(size_t)(nb + b)] = be - bs;
+    }
+    int64_t* dtab = nullptr;
+    int rc = ws_alloc((void**)&dtab, tab.size() * 8, s);
+    if (rc != PS_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(dtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaStream_t sc = nullptr;
+    const int64_t G = std::max<int64_t>(1, (nb + 7) / 8);  // blocks per group: about 8 groups
+    const int64_t ng = (nb + G - 1) / G;
+    std::vector<cudaEvent_t> ev((size_t)ng + 1, nullptr);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking);
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    // the copies start once the device buffer exists on s
+    if (e == cudaSuccess) e = cudaEventRecord(ev[(size_t)ng], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, ev[(size_t)ng], 0);
+    for (int64_t g = 0; g < ng && e == cudaSuccess && rc == PS_OK; g++) {
+        const int64_t b0 = g * G, b1 = std::min(nb, b0 + G);
+        const int64_t k0 = std::min(b0 * L, n), k1 = std::min(b1 * L, n);
+        if (k1 > k0)
+            e = cudaMemcpyAsync((char*)d + k0 * kb, (const char*)host_keys + k0 * kb, (size_t)(k1 - k0) * kb,
+                                cudaMemcpyHostToDevice, sc);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[(size_t)g], sc);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[(size_t)g], 0);
+        if (e != cudaSuccess || k1 <= k0) continue;
+        SortArgs a;
+        a.keys = d;
+        a.payload = nullptr;
+        a.n = L;
+        a.dtype = dtype;
+        a.mode = mode;
+        a.n_B = a.n_P = 1;
+        a.items = r.items_per_thread;
+        a.threads = r.block_threads;
+        a.trace = nullptr;
+        a.stream = s;
+        a.inst_base = dtab + b0;
+        a.inst_n = dtab + nb + b0;
+        a.n_inst = b1 - b0;
+        a.n_max = L;
+        a.n_sum = k1 - k0;
+        a.extent = n;
+        a.keep_order_keys = true;
+        rc = dispatch(a);
+    }
+    if (e == cudaSuccess && rc == PS_OK) {
+        SortArgs a;  // steps 2 to 4 on the sorted blocks, result into the host buffer
+        a.keys = d;
+        a.payload = nullptr;
+        a.n = n;
+        a.dtype = dtype;
+        a.mode = mode;
+        a.n_B = nb;
+        a.n_P = r.n_parts;
+        a.merge_variant = (int)r.merge_variant;
+        a.items = r.items_per_thread;
+        a.threads = r.block_threads;
+        a.trace = nullptr;
+        a.stream = s;
+        a.dst_keys = mapped;
+        a.presorted = true;
+        rc = dispatch(a);
+    }
+    // the caller waits for s; the copy stream's work is ordered before s's
+    // sorts by the events, so both are done once s is
+    if (sc) cudaStreamDestroy(sc);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    ws_free(dtab, s);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return rc;
+}
+
 }  // namespace ps
 
 using namespace ps;
@@ -835,9 +929,11 @@ int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode, const ps
     rc = ws_alloc(&d, bytes, s);
     if (rc != PS_OK) return rc;
     cudaError_t e = cudaSuccess;
-    if (mapped) {
-        ps_params r;
-        resolve(n, dtype, params, &r);
+    ps_params r;
+    resolve(n, dtype, params, &r);
+    if (mapped && r.n_blocks > 1 && n >= HOST_PIPE_MIN) {
+        rc = host_pipelined(host_keys, mapped, d, n, dtype, pivot_mode, r, s);
+    } else if (mapped) {
         SortArgs a;
         a.keys = d;
         a.payload = nullptr;

@@ -41,6 +41,12 @@ struct SortArgs {
     // scratch for the passes in between.  nullptr: both are `keys`.
     const void* src_keys = nullptr;
     void* dst_keys = nullptr;
+    // The block sort's last pass keeps the order keys (no inverse transform):
+    // used to sort the blocks of a larger sort ahead of its steps 2 to 4.
+    bool keep_order_keys = false;
+    // Step 1 is done already: `keys` holds every block of the sort sorted, as
+    // order keys; the call runs steps 2 to 4 only (dst_keys must be given).
+    bool presorted = false;
 };
 
 // Workspace from the library's stream-ordered pool.

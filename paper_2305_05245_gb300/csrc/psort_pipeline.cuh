@@ -338,8 +338,8 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
     {
         // the tile sort is the whole sort when there is one block, one
         // partition and no in-block pass
-        auto f = (pl.direct && pl.npass == 0) ? k_tile_sort<TNT, TE, K, XF, true, C::TW>
-                                              : k_tile_sort<TNT, TE, K, XF, false, C::TW>;
+        const bool fin = pl.direct && pl.npass == 0 && !a_.keep_order_keys;
+        auto f = fin ? k_tile_sort<TNT, TE, K, XF, true, C::TW> : k_tile_sort<TNT, TE, K, XF, false, C::TW>;
         cudaError_t e = smem_attr(f, tile_smem());
         if (e != cudaSuccess) return e;
         const int64_t grid = pl.n_inst * pl.n_B * pl.R0;
@@ -447,13 +447,15 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
         // Step 1: sort each block (tiles, then in-block merge passes).  The
         // passes alternate between the caller's buffer and the workspace copy;
         // the block sort ends in the workspace, or in the caller's buffer when
-        // it is the whole sort (one block, one partition).
+        // it is the whole sort (one block, one partition).  Presorted: the
+        // caller's buffer already holds the sorted blocks (order keys).
         const bool end_in_user = pl.direct;
         GBuf<K> cur = ((pl.npass % 2 == 0) != end_in_user) ? wsb : user;
         if (end_in_user && pl.npass == 0) cur = last;
-        if ((e = tile_sort<XF>(first, cur, pl, a, s)) != cudaSuccess) return e;
+        if (a.presorted) cur = user;
+        else if ((e = tile_sort<XF>(first, cur, pl, a, s)) != cudaSuccess) return e;
         int64_t W = T;
-        for (int p = 0; p < pl.npass; p++) {
+        for (int p = 0; p < pl.npass && !a.presorted; p++) {
             MergeJob job{};  // in-block pass p
             job.kind = 0;
             job.K = (int)pl.F[p];
@@ -465,7 +467,7 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
             job.gpb = (Rp + pl.F[p] - 1) / pl.F[p];
             GBuf<K> nxt = same_buf(cur, wsb) ? user : wsb;
             if (p + 1 == pl.npass && end_in_user) nxt = last;
-            if (p + 1 == pl.npass && end_in_user) {
+            if (p + 1 == pl.npass && end_in_user && !a.keep_order_keys) {
                 if ((e = merge<XF>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) return e;
             } else if ((e = merge<0>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) {
                 return e;

@@ -30,6 +30,11 @@ CASES = [
     (1_000_003, "uint64", "uniform", 0, 0),
     (3_000_017, "int32", "reverse", 2, 8),
     (2_000_000, "float64", "uniform", 0, 0),
+    # 2^24 keys and more in pinned memory take the pipelined path: blocks copied
+    # in groups while earlier groups are block-sorted, then steps 2 to 4
+    ((1 << 24) + 12_345, "int64", "uniform", 0, 0),
+    (20_000_003, "float32", "gaussian", 48, 96),
+    ((1 << 24) + 1, "int32", "few_unique", 7, 3),
 ]
 
 
@@ -40,6 +45,8 @@ def test_sort_host(ps, ora, n, dtype, dist, n_B, n_P, pinned, mode):
     import torch
     if dist == "gaussian" and not dtype.startswith("float"):
         pytest.skip("gaussian keys are floating point")
+    if n >= (1 << 24) and not pinned:
+        pytest.skip("large cases are for the pinned (pipelined) path")
     keys = synth.keys(n, dtype, dist, seed=synth.seed_for("host", n, dtype, dist))
     want = ora.reference_sort(keys)
     if pinned:
