@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--serial-fraction", type=float, default=0.25,
                     help="serve: leading fraction of the trace replayed through serial per-request ps_sort")
     ap.add_argument("--segments", type=int, default=20000)
-    ap.add_argument("--baseline-segments", type=int, default=2000,
+    ap.add_argument("--baseline-segments", type=int, default=None,
                     help="segments timed with one ps_sort call each (batch workload)")
     a = ap.parse_args()
     if a.n is None and a.workload not in ("table1", "merge_ablation"):
@@ -330,7 +330,7 @@ def run_batch(a):
     except Exception as ex:  # reported, not fatal: the main line stands
         graph = {"error": str(ex)[:200]}
     # the plain path: one ps_sort per segment, on the first baseline-segments segments
-    nb = min(a.baseline_segments, a.segments)
+    nb = a.segments if a.baseline_segments is None else min(a.baseline_segments, a.segments)
     keys.copy_(pristine)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -359,6 +359,7 @@ def run_batch(a):
                                 "keys_per_s": base_keys / (base_ms / 1e3)},
         "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in prof.items()},
         "gpu_launches": sum(v[0] for v in prof.values()),
+        "launches_per_batch": sum(v[0] for v in prof.values()) / a.steps,
         "clocks": clk.summary(), "check": "ok" if ok else "FAILED",
     }
     print(json.dumps(line))

@@ -695,11 +695,19 @@ static int autotune(int dtype, int mode, int64_t n_min, int64_t n_max, int batch
 // travel to the device in groups of blocks on a copy stream while the blocks
 // that have arrived are sorted (one batched block sort per group: every block
 // an instance with one block and one partition, its result kept as order
-// keys).  Steps 2 to 4 then run on the sorted blocks and the final merge
-// writes the result straight into the host buffer.  The host link (about
-// 0.2 TB/s each way on GB300) is the bound; this hides the block sort's
-// merge passes behind the transfer instead of running them after it.
+// keys).  Steps 2 to 4 then run on the sorted blocks.  Exact splitting fixes
+// every partition's offset in advance, so the final merge runs over ranges of
+// partitions into device memory and each range is copied back while the next
+// is merged; regular sampling's final merge writes straight into the host
+// buffer.  The host link (about 0.2 TB/s each way on GB300) is the bound; this
+// hides the block sort and the final merge behind the transfers.
 static constexpr int64_t HOST_PIPE_MIN = int64_t(1) << 24;
+#ifndef PS_HOST_GROUPS
+#define PS_HOST_GROUPS 8   // block groups copied in while earlier ones sort
+#endif
+#ifndef PS_HOST_RANGES
+#define PS_HOST_RANGES 8   // partition ranges copied out while later ones merge
+#endif
 
 static int host_pipelined(const void* host_keys, void* mapped, void* d, int64_t n, int dtype, int mode,
                           const ps_params& r, cudaStream_t s)
@@ -718,7 +726,7 @@ static int host_pipelined(const void* host_keys, void* mapped, void* d, int64_t 
     if (rc != PS_OK) return rc;
     cudaError_t e = cudaMemcpyAsync(dtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s);
     cudaStream_t sc = nullptr;
-    const int64_t G = std::max<int64_t>(1, (nb + 7) / 8);  // blocks per group: about 8 groups
+    const int64_t G = std::max<int64_t>(1, (nb + PS_HOST_GROUPS - 1) / PS_HOST_GROUPS);  // blocks per group
     const int64_t ng = (nb + G - 1) / G;
     std::vector<cudaEvent_t> ev((size_t)ng + 1, nullptr);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking);
@@ -756,6 +764,9 @@ static int host_pipelined(const void* host_keys, void* mapped, void* d, int64_t 
         a.keep_order_keys = true;
         rc = dispatch(a);
     }
+    void* d2 = nullptr;  // the final merge's device output (exact splitting)
+    if (e == cudaSuccess && rc == PS_OK && mode == PS_PIVOT_EXACT && PS_HOST_RANGES > 1)
+        rc = ws_alloc(&d2, (size_t)n * kb, s);
     if (e == cudaSuccess && rc == PS_OK) {
         SortArgs a;  // steps 2 to 4 on the sorted blocks, result into the host buffer
         a.keys = d;
@@ -770,10 +781,14 @@ static int host_pipelined(const void* host_keys, void* mapped, void* d, int64_t 
         a.threads = r.block_threads;
         a.trace = nullptr;
         a.stream = s;
-        a.dst_keys = mapped;
+        a.dst_keys = d2 ? d2 : mapped;
+        a.host_out = d2 ? const_cast<void*>(host_keys) : nullptr;
+        a.copy_stream = d2 ? sc : nullptr;
+        a.out_ranges = PS_HOST_RANGES;
         a.presorted = true;
         rc = dispatch(a);
     }
+    if (d2) ws_free(d2, s);
     // the caller waits for s; the copy stream's work is ordered before s's
     // sorts by the events, so both are done once s is
     if (sc) cudaStreamDestroy(sc);

@@ -47,6 +47,14 @@ struct SortArgs {
     // Step 1 is done already: `keys` holds every block of the sort sorted, as
     // order keys; the call runs steps 2 to 4 only (dst_keys must be given).
     bool presorted = false;
+    // Exact splitting, one instance: step 4 runs over out_ranges ranges of
+    // partitions into dst_keys (device), and each range's output is copied to
+    // host_out on copy_stream as soon as it is merged (partition k starts at
+    // floor(k*n/n_P), known on the host).  The caller's stream waits for the
+    // copies.
+    void* host_out = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    int out_ranges = 0;
 };
 
 // Workspace from the library's stream-ordered pool.

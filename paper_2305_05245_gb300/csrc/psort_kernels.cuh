@@ -856,6 +856,7 @@ struct MergeJob {
     const int64_t* splits;           // kind 1: rows (inst*n_B + b), n_P+1 columns
     const int64_t* offsets;          // kind 1: rows inst, n_P+1 absolute offsets
     int64_t n_P;                     // kind 1
+    int64_t k0;                      // kind 1, one instance: group g is partition k0 + g
     __device__ __forceinline__ void run(int64_t g, int r, int64_t& lo, int64_t& hi) const
     {
         if (kind == 0) {
@@ -867,7 +868,7 @@ struct MergeJob {
             lo = o + (s < be ? s : be);
             hi = o + (s + W < be ? s + W : be);
         } else {
-            const int64_t inst = g / n_P, k = g - inst * n_P;
+            const int64_t inst = g / n_P, k = g - inst * n_P + k0;
             int64_t bs, be;
             block_bounds(in.len(inst), n_B, r, bs, be);
             const int64_t* row = splits + (inst * n_B + r) * (n_P + 1);
@@ -885,7 +886,7 @@ struct MergeJob {
             const int64_t s = bs + gi * K * W;
             return in.off(inst) + (s < be ? s : be);
         }
-        const int64_t inst = g / n_P, k = g - inst * n_P;
+        const int64_t inst = g / n_P, k = g - inst * n_P + k0;
         return offsets[inst * (n_P + 1) + k];
     }
     // number of elements of group g
@@ -899,7 +900,7 @@ struct MergeJob {
             const int64_t s = out_base(g), e = s + (int64_t)K * W, end = in.off(inst) + be;
             return (e < end ? e : end) - s;
         }
-        const int64_t inst = g / n_P, k = g - inst * n_P;
+        const int64_t inst = g / n_P, k = g - inst * n_P + k0;
         return offsets[inst * (n_P + 1) + k + 1] - offsets[inst * (n_P + 1) + k];
     }
 };

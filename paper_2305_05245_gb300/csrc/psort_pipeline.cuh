@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "psort_internal.h"
@@ -243,6 +244,10 @@ template <> inline GBuf<uint64_t> gbuf_ext<uint64_t>(const void* p, const GBuf<u
 }
 template <> inline GBuf<Rec> gbuf_ext<Rec>(const void*, const GBuf<Rec>& f) { return f; }
 
+// Base address of a keys-only buffer (records have no single base).
+template <typename K> static const void* last_ptr(const GBuf<K>& b) { return b.p; }
+template <> inline const void* last_ptr<Rec>(const GBuf<Rec>& b) { return b.k; }
+
 template <typename K> static bool same_buf(const GBuf<K>& x, const GBuf<K>& y);
 template <> inline bool same_buf<uint32_t>(const GBuf<uint32_t>& x, const GBuf<uint32_t>& y) { return x.p == y.p; }
 template <> inline bool same_buf<uint64_t>(const GBuf<uint64_t>& x, const GBuf<uint64_t>& y) { return x.p == y.p; }
@@ -353,9 +358,12 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
     // one CTA per final group.
     // variant: ps_merge_variant of the last level's chunk merge.
     template <int XF>
+    // G0: groups of the job (default: the shape's capacity, every group).
     static cudaError_t merge(const MergeJob& job, const MergeShape& sh, GBuf<K> src, GBuf<K> dst,
-                             const PlanK& pl, char* ws, cudaStream_t s, int variant = PS_MERGE_TREE)
+                             const PlanK& pl, char* ws, cudaStream_t s, int variant = PS_MERGE_TREE,
+                             int64_t G0 = -1)
     {
+        if (G0 < 0) G0 = sh.G[0];
         const bool fin = job.kind == 1;
         char* m = ws + pl.o_merge;
         const int Kr = sh.K;
@@ -372,8 +380,8 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
         cudaError_t e;
         {
             ProfScope ps_(fin ? "windows_final" : "windows_inblock", s);
-            const int64_t nt = sh.G[0] * Kr;
-            k_root_windows<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(job, sh.G[0], Lv[0]);
+            const int64_t nt = G0 * Kr;
+            k_root_windows<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(job, G0, Lv[0]);
         }
         auto fp = k_pool<PNT, PE, K, PS_POOL_SPC>;
         if ((e = smem_attr(fp, pool_smem(Kr))) != cudaSuccess) return e;
@@ -528,7 +536,37 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
         job.splits = splits;
         job.offsets = offs;
         job.n_P = pl.n_P;
-        if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, last, pl, ws, s, a.merge_variant)) != cudaSuccess) return e;
+        if (!pl.direct && !std::is_same<K, Rec>::value && a.host_out && a.copy_stream && a.out_ranges > 1 &&
+            pl.n_inst == 1 && a.mode == PS_PIVOT_EXACT) {
+            // partition ranges, each copied out while the next is merged
+            const int64_t nr = std::min<int64_t>(a.out_ranges, pl.n_P);
+            const size_t kb = GStore<K>::bytes;
+            auto start = [&](int64_t k) { return (int64_t)(((unsigned __int128)k * (uint64_t)pl.N) / (uint64_t)pl.n_P); };
+            for (int64_t r = 0; r < nr && e == cudaSuccess; r++) {
+                const int64_t k0 = r * pl.n_P / nr, k1 = (r + 1) * pl.n_P / nr;
+                job.k0 = k0;
+                if ((e = merge<XF>(job, pl.fin, cur, last, pl, ws, s, a.merge_variant, k1 - k0)) != cudaSuccess) break;
+                cudaEvent_t ev;
+                if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) break;
+                e = cudaEventRecord(ev, s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(a.copy_stream, ev, 0);
+                const int64_t o0 = start(k0), o1 = start(k1);
+                if (e == cudaSuccess && o1 > o0)
+                    e = cudaMemcpyAsync((char*)a.host_out + o0 * kb, (const char*)last_ptr(last) + o0 * kb,
+                                        (size_t)(o1 - o0) * kb, cudaMemcpyDeviceToHost, a.copy_stream);
+                cudaEventDestroy(ev);
+            }
+            if (e != cudaSuccess) return e;
+            // the caller's stream completes after the last copy
+            cudaEvent_t done;
+            if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess) return e;
+            e = cudaEventRecord(done, a.copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done, 0);
+            cudaEventDestroy(done);
+            if (e != cudaSuccess) return e;
+        } else if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, last, pl, ws, s, a.merge_variant)) != cudaSuccess) {
+            return e;
+        }
         // Trace (single sorts only).
         if (a.trace && pl.n_inst == 1) {
             const ps_trace* t = a.trace;
