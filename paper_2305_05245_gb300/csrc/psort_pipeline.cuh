@@ -253,6 +253,23 @@ template <> inline bool same_buf<uint32_t>(const GBuf<uint32_t>& x, const GBuf<u
 template <> inline bool same_buf<uint64_t>(const GBuf<uint64_t>& x, const GBuf<uint64_t>& y) { return x.p == y.p; }
 template <> inline bool same_buf<Rec>(const GBuf<Rec>& x, const GBuf<Rec>& y) { return x.k == y.k; }
 
+// Profiler label of planning kernel `what` (0 chunk plan, 1 sample pool, 2
+// co-ranks, 3 child windows) at refinement level l of an in-block or final
+// merge job.
+static inline const char* level_label(bool fin, int what, int l)
+{
+    static const char* const names[2][4][3] = {
+        {{"plan_inblock_l1", "plan_inblock_l2", "plan_inblock_l3"},
+         {"pool_inblock_l1", "pool_inblock_l2", "pool_inblock_l3"},
+         {"corank_inblock_l1", "corank_inblock_l2", "corank_inblock_l3"},
+         {"children_inblock_l1", "children_inblock_l2", "children_inblock_l3"}},
+        {{"plan_final_l1", "plan_final_l2", "plan_final_l3"},
+         {"pool_final_l1", "pool_final_l2", "pool_final_l3"},
+         {"corank_final_l1", "corank_final_l2", "corank_final_l3"},
+         {"children_final_l1", "children_final_l2", "children_final_l3"}}};
+    return names[fin ? 1 : 0][what][l < 2 ? l : 2];
+}
+
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel) to
 // the largest size asked so far, so that launches queued later (for example
 // while a stream is being captured into a CUDA graph) make no attribute call.
@@ -390,21 +407,21 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
             int* chgrp = (int*)(m + sh.o_chgrp[l]);
             Splitter<K>* spl = (Splitter<K>*)(m + sh.o_spl[l]);
             {
-                ProfScope ps_(fin ? "plan_final" : "plan_inblock", s);
+                ProfScope ps_(level_label(fin, 0, l), s);
                 k_chunk_plan<1024><<<1, 1024, 0, s>>>(Lv[l], sh.cnom[l], sh.jcap, choff);
             }
             {
-                ProfScope ps_(fin ? "pool_final" : "pool_inblock", s);
+                ProfScope ps_(level_label(fin, 1, l), s);
                 fp<<<(unsigned)sh.G[l], PNT, pool_smem(Kr), s>>>(Lv[l], src, choff, chgrp, spl, sh.G[l + 1],
                                                                  Lv[l + 1]);
             }
             {
-                ProfScope ps_(fin ? "corank_final" : "corank_inblock", s);
+                ProfScope ps_(level_label(fin, 2, l), s);
                 const int64_t nt = sh.G[l + 1] * Kr;
                 k_corank<K><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(Lv[l], src, spl, choff, chgrp, Lv[l + 1]);
             }
             {
-                ProfScope ps_(fin ? "children_final" : "children_inblock", s);
+                ProfScope ps_(level_label(fin, 3, l), s);
                 k_child_stats<256><<<(unsigned)((sh.G[l + 1] + 7) / 8), 256, 0, s>>>(Lv[l], choff, chgrp, Lv[l + 1]);
             }
         }
