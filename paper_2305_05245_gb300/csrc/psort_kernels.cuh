@@ -1066,12 +1066,13 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
         if (q > last) q = last;
         if (!PS_IN(q, last + 1, 24)) continue;
         cp_elem(pool.kb, i, src, lo[x] + q);
-        pool.tb.st(i, ((uint64_t)x << 32) | (uint64_t)q);
+        pool.tb.st(i, ((uint64_t)x << 32) | (uint64_t)(i - off[x]));  // run, ordinal in the run
     }
     cp_async_wait_all();
     __syncthreads();
     merge_pieces<NT, E>(pool, off, Kr, P);
-    // weights: a sample stands for S keys, or for the shorter last block of its run
+    // weights: sample o of run x (ordinal o, at position min(o*S + S-1, len-1))
+    // stands for S keys, or for the len - o*S keys of its run's last block
     const int q0 = threadIdx.x * E;
     int64_t wsum = 0;
 #pragma unroll
@@ -1080,9 +1081,9 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
             const uint64_t tag = pool.tb.ld(q0 + i);
             const int x = (int)(tag >> 32);
             if (!PS_IN(x, Kr, 25)) continue;
-            const int64_t q = (int64_t)(uint32_t)tag, len = hi[x] - lo[x];
-            wsum += (q == len - 1 && len % S) ? len % S : S;
-            const int64_t slot = off[x] + q / S;  // the sample's ordinal within its run
+            const int64_t o = (int64_t)(uint32_t)tag, len = hi[x] - lo[x];
+            wsum += o == off[x + 1] - off[x] - 1 ? len - o * S : S;
+            const int64_t slot = off[x] + o;
             if (PS_IN(slot, off[x + 1], 36) && slot < off[x + 1]) mpos[slot] = q0 + i;
         }
     }
@@ -1091,29 +1092,42 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
     // A splitter's co-rank exceeds its cumulative weight by the partial block
     // of every other run, (S-1)/2 keys on average: aim the weights that much lower.
     const int64_t adj = (int64_t)(Kr - 1) * (S - 1) / 2;
+    // Splitter j goes to the sample whose cumulative weight range (cb, ci]
+    // holds its target t_j = max(1, floor(j*M/J) - adj).  The targets grow with
+    // j, so each thread walks them along its samples: the first j with
+    // t_j > cb comes from one division (for cb >= 1 only unclamped targets
+    // qualify, and those satisfy j >= (cb + adj + 1) * J / M), later ones from
+    // floor((j+1)*M/J) = floor(j*M/J) + floor(M/J) + carry of the remainders.
+    int64_t j = 1;
+    if (cb > 0) {
+        j = muldiv(cb + adj + 1, J, M) - 1;
+        if (j < 1) j = 1;
+    }
+    const int64_t Mq = M / J, Mr = M - Mq * J;
+    int64_t qj = muldiv(j, M, J), rj = j * M - qj * J;
 #pragma unroll
     for (int i = 0; i < E; i++) {
         if (q0 + i < P) {
             const Tagged<K> e = pool.ld(q0 + i);
             const int x = (int)(e.tag >> 32);
             if (!PS_IN(x, Kr, 26)) continue;
-            const int64_t q = (int64_t)(uint32_t)e.tag, len = hi[x] - lo[x];
-            const int64_t ci = cb + ((q == len - 1 && len % S) ? len % S : S);
-            // splitters j whose target t_j = max(1, floor(j*M/J) - adj) lies in
-            // (cb, ci]; for cb >= 1 only unclamped targets qualify, and those
-            // satisfy j >= (cb + adj + 1) * J / M
-            int64_t j = 1;
-            if (cb > 0) {
-                j = muldiv(cb + adj + 1, J, M) - 1;
-                if (j < 1) j = 1;
-            }
+            const int64_t o = (int64_t)(uint32_t)e.tag, len = hi[x] - lo[x];
+            const bool lastblk = o == off[x + 1] - off[x] - 1;
+            const int64_t ci = cb + (lastblk ? len - o * S : S);
             for (; j < J; j++) {
-                int64_t t = muldiv(j, M, J) - adj;
+                int64_t t = qj - adj;
                 if (t < 1) t = 1;
                 if (t > ci) break;
                 if (t > cb) {
+                    const int64_t q = lastblk ? len - 1 : o * S + (S - 1);
                     spl[c0 + j] = Splitter<K>{e.key, (uint32_t)x, (uint32_t)q};
                     if (j <= POOL / 2) jpos[j] = q0 + i;
+                }
+                qj += Mq;
+                rj += Mr;
+                if (rj >= J) {
+                    rj -= J;
+                    qj++;
                 }
             }
             cb = ci;
@@ -1148,6 +1162,9 @@ __global__ void __launch_bounds__(NT) k_pool(Level L, GBuf<K> src, const int64_t
 // c starts in run r: runs before the splitter's run contribute their
 // elements <= key, runs after it their elements < key, the splitter's own run
 // everything up to and including the splitter.  Writes the child level's lo.
+// One thread per (child, run) pair: its binary search touches a few 32-byte
+// sectors of the window, and the kernel runs near DRAM bandwidth (a warp per
+// pair reading whole windows was measured 4x slower).
 template <typename K>
 __global__ void k_corank(Level L, GBuf<K> src, const Splitter<K>* spl, const int64_t* choff, const int* chgrp,
                          Level C)
