@@ -811,6 +811,12 @@ def main():
         tuned = True
     nb, np_ = ps.resolve_params(n, {"int32": 0, "int64": 1, "float32": 2, "float64": 3,
                                     "uint32": 4, "uint64": 5}[a.dtype], a.n_blocks, a.n_parts)
+    # launch shape: the tuned entry's when the autotuner ran, else the automatic one
+    shape = "automatic"
+    if tuned:
+        ent = ps.autotune_table(a.dtype).get(max(0, round(np.log2(n))))
+        if ent and ent[2]:
+            shape = "%d threads x %d keys" % (ent[3] or 256, ent[2] or 32)
 
     def step():
         ps.sort(keys, a.pivot, n_blocks=a.n_blocks, n_parts=a.n_parts, merge_variant=a.merge_variant)
@@ -894,7 +900,8 @@ def main():
                                        "float64": "f64", "uint32": "u32", "uint64": "u64"}[a.dtype],
         "data": "synthetic (SplitMix64, seeded), resident in HBM",
         "config": {"workload": wl, "n": n, "dist": a.dist, "pivot": a.pivot, "n_blocks": nb,
-                   "n_parts": np_, "params": "autotuned (ps_autotune, untimed)" if tuned else
+                   "n_parts": np_, "launch_shape": shape,
+                   "params": "autotuned (ps_autotune, untimed)" if tuned else
                    ("explicit" if a.n_blocks or a.n_parts else "library defaults (measured size table)"),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (no flush needed)",
