@@ -387,12 +387,15 @@ struct BatchBin {
 struct BatchPlan {
     int dtype = 0, mode = 0;
     int64_t extent = 0;
+    bool own = false;            // segments in buffers of their own (per bin: starts, lengths, pointers)
     std::vector<int64_t> table;  // host copy of the instance table
     std::vector<BatchBin> bins;
 };
 
+// own (optional): one device pointer per segment; segment i then lives in its
+// own buffer, and off only lays the segments out for the workspace.
 static int batch_make_plan(const std::vector<int64_t>& off, int dtype, int mode, const ps_params* force,
-                           BatchPlan* bp)
+                           BatchPlan* bp, const std::vector<void*>* own = nullptr)
 {
     const int64_t n_segs = (int64_t)off.size() - 1;
     if (dtype < PS_I32 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
@@ -402,6 +405,8 @@ static int batch_make_plan(const std::vector<int64_t>& off, int dtype, int mode,
     bp->dtype = dtype;
     bp->mode = mode;
     bp->extent = off[(size_t)n_segs];
+    bp->own = own != nullptr;
+    if (own && own->size() < (size_t)n_segs) return PS_ERR_INVALID_ARG;
     bp->table.clear();
     bp->bins.clear();
     // bins: 0 = at most SMALL_SEG keys (one small CTA each); 1 = fits one
@@ -429,6 +434,8 @@ static int batch_make_plan(const std::vector<int64_t>& off, int dtype, int mode,
             bb.nmax = std::max<int64_t>(bb.nmax, len);
             bb.nsum += len;
         }
+        if (own)
+            for (int64_t i : bins[b]) bp->table.push_back((int64_t)(uintptr_t)(*own)[(size_t)i]);
         ps_params r;
         memset(&r, 0, sizeof(r));
         if (b <= 1) {
@@ -465,6 +472,7 @@ static SortArgs batch_bin_args(const BatchPlan& bp, const BatchBin& bb, const in
     a.stream = s;
     a.inst_base = dev_table + bb.at;
     a.inst_n = dev_table + bb.at + bb.cnt;
+    if (bp.own && dev_table) a.inst_ptrs = (void* const*)(dev_table + bb.at + 2 * bb.cnt);
     a.n_inst = bb.cnt;
     a.n_max = bb.nmax;
     a.n_sum = bb.nsum;
@@ -500,14 +508,14 @@ static int batch_launch(const BatchPlan& bp, const int64_t* dev_table, void* key
 // Batched sort of the segments [off[i], off[i+1]) of `keys` (host offsets):
 // bins by length, one multi-instance pipeline per bin, queued on s.
 int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
-               int64_t* pinned, size_t pinned_cap, const ps_params* force)
+               int64_t* pinned, size_t pinned_cap, const ps_params* force, const std::vector<void*>* own)
 {
     if ((int64_t)off.size() - 1 <= 0) return PS_OK;
     if (dtype < PS_I32 || dtype > PS_U64) return PS_ERR_UNSUPPORTED;
     if (!keys) return PS_ERR_INVALID_ARG;
     if ((uintptr_t)keys % (narrow_dtype(dtype) ? 4 : 8) != 0) return PS_ERR_INVALID_ARG;
     BatchPlan bp;
-    int rc = batch_make_plan(off, dtype, mode, force, &bp);
+    int rc = batch_make_plan(off, dtype, mode, force, &bp, own);
     if (rc != PS_OK) return rc;
     const size_t total = bp.table.size();
     if (total == 0) return PS_OK;

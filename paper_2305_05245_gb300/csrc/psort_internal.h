@@ -55,6 +55,12 @@ struct SortArgs {
     void* host_out = nullptr;
     cudaStream_t copy_stream = nullptr;
     int out_ranges = 0;
+    // Batched keys-only sorts whose instances live in buffers of their own:
+    // device table of one device pointer per instance (in instance-table
+    // order).  The first pass reads each instance from its buffer and the
+    // last pass writes it back there; `keys` (extent keys, laid out by
+    // inst_base) only carries the passes in between.
+    void* const* inst_ptrs = nullptr;
 };
 
 // Workspace from the library's stream-ordered pool.
@@ -92,8 +98,13 @@ int viol_read_rec(unsigned long long* out);
 // pinned (optional): page-locked host scratch of pinned_cap int64 for the
 // instance table; when given, the call does not wait for the stream.
 // force (optional): n_B/n_P for every bin above the one-tile bin (tuning).
+// own (optional, keys-only): one device pointer per segment; each segment is
+// then read from and written back to its own buffer, and keys only carries
+// the passes in between (off lays the segments out in it).  The instance
+// table then holds 3 int64 per segment instead of 2.
 int batch_sort(const std::vector<int64_t>& off, void* keys, int dtype, int mode, cudaStream_t s,
-               int64_t* pinned, size_t pinned_cap, const ps_params* force = nullptr);
+               int64_t* pinned, size_t pinned_cap, const ps_params* force = nullptr,
+               const std::vector<void*>* own = nullptr);
 // The size heuristic alone (no tuned entries), with every field automatic.
 void resolve_default(int64_t n, int dtype, ps_params* out);
 // Records (uint64 key, uint32 payload) through the validated record path.

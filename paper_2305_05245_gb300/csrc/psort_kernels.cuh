@@ -712,6 +712,18 @@ struct Inst {
     int64_t n0;           // length of the single instance when base is null
     __device__ __forceinline__ int64_t off(int64_t i) const { return base ? base[i] : 0; }
     __device__ __forceinline__ int64_t len(int64_t i) const { return base ? n[i] : n0; }
+    // The instance holding absolute position x (instances at increasing offsets).
+    __device__ __forceinline__ int64_t find(int64_t x) const
+    {
+        if (!base) return 0;
+        int64_t a = 0, b = count - 1;
+        while (a < b) {
+            const int64_t m = (a + b + 1) >> 1;
+            if (base[m] <= x) a = m;
+            else b = m - 1;
+        }
+        return a;
+    }
 };
 
 // Bounds [bs, be) of block b (relative to its instance) for instance length N.
@@ -790,9 +802,12 @@ __device__ __forceinline__ void tile_load_regs(const GBuf<K>& src, int64_t o, in
 // warp-shuffle merge levels, then shared-memory merge-path levels for the
 // rest.  Records: cp.async staging through shared memory, then the same
 // network and shared-memory levels.
+// iptr (plain keys, batches): instance i's keys live in their own buffer
+// iptr[i] (in the compact layout they would start at in.off(i)); the tile is
+// read from there and, when FINAL, written back there.
 template <int NT, int E, typename K, int XF, bool FINAL, int WLEV = 0>
 __global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
-    k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst in, int64_t n_B, int64_t R0)
+    k_tile_sort(GBuf<K> src, GBuf<K> dst, Inst in, int64_t n_B, int64_t R0, K* const* iptr)
 {
     constexpr int T = NT * E;
     constexpr bool PLAIN = sizeof(K) == 4 || sizeof(K) == 8;
@@ -815,7 +830,12 @@ __global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
     const int n = (int)(be - ts < T ? be - ts : T);
     K r[E];
     if constexpr (PLAIN) {
-        tile_load_regs<NT, E, K, XF>(src, o, n, r);
+        if (iptr) {
+            const GBuf<K> own{iptr[inst] + ts, (int64_t)n};
+            tile_load_regs<NT, E, K, XF>(own, 0, n, r);
+        } else {
+            tile_load_regs<NT, E, K, XF>(src, o, n, r);
+        }
     } else {
         for (int i = threadIdx.x; i < n; i += NT) cp_elem(sb, i, src, o + i);
         cp_async_wait_all();
@@ -832,6 +852,13 @@ __global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
     store_bitonic<E>(SV{sb}, threadIdx.x * E, E << WLEV, (E << WLEV) >= T, r);
     __syncthreads();
     merge_levels_pow2<NT, E>(SV{sb}, E << (WLEV + 1));
+    if constexpr (PLAIN && FINAL) {
+        if (iptr) {
+            const GBuf<K> own{iptr[inst] + ts, (int64_t)n};
+            for (int i = threadIdx.x; i < n; i += NT) own.template stx<XF>(i, sb.ld(i));
+            return;
+        }
+    }
     for (int i = threadIdx.x; i < n; i += NT) {
         if (FINAL) dst.template stx<XF>(o + i, sb.ld(i));
         else dst.st(o + i, sb.ld(i));
@@ -1347,9 +1374,12 @@ __device__ void exact_corank(const GBuf<K>& src, const int64_t* a, const int64_t
 // SORTCHUNK (non-BIG only): the pieces are copied side by side and the chunk
 // is sorted as a whole, ignoring that the pieces are sorted (the "copy and
 // sort" way of multiway merging, Sec. 2.2).
+// iptr (plain keys, batches): the output goes to the instances' own buffers
+// instead of dst; a group never straddles two instances, so each chunk finds
+// its instance once (in) and writes iptr[i] + (position - in.off(i)).
 template <int NT, int E, typename K, int XF, bool BIG, bool ALIGNED, bool SORTCHUNK = false>
 __global__ void __launch_bounds__(NT, (BIG ? 1 : data_ctas<K, NT, E>())) k_merge(Level C, GBuf<K> src, GBuf<K> dst, int64_t nout, int64_t* big,
-                                              unsigned long long* nbig)
+                                              unsigned long long* nbig, K* const* iptr, Inst in)
 {
     static_assert(!(BIG && ALIGNED), "the oversized-group path merges unpadded pieces");
     static_assert(!(SORTCHUNK && (BIG || ALIGNED)), "copy-and-sort chunks are unpadded and fit the capacity");
@@ -1443,7 +1473,17 @@ __global__ void __launch_bounds__(NT, (BIG ? 1 : data_ctas<K, NT, E>())) k_merge
             } else {
                 merge_pieces<NT, E>(SV{sb}, off, Kr, (int)take);
             }
-            for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
+            bool own_done = false;
+            if constexpr (sizeof(K) == 4 || sizeof(K) == 8) {
+                if (iptr) {
+                    const int64_t ii = in.find(out);
+                    const GBuf<K> own{iptr[ii] + (out - in.off(ii)), take};
+                    for (int i = threadIdx.x; i < (int)take; i += NT) own.template stx<XF>(i, sb.ld(i));
+                    own_done = true;
+                }
+            }
+            if (!own_done)
+                for (int i = threadIdx.x; i < (int)take; i += NT) dst.template stx<XF>(out + i, sb.ld(i));
             out += take;
             M -= take;
             if constexpr (BIG) {

@@ -345,6 +345,13 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
     }
     static size_t tile_smem() { return TileBuf<K, TE>::type::bytes(T) + 64; }
 
+    // The instances' own buffers (plain keys only).
+    static K* const* iptrs(const SortArgs& a)
+    {
+        if constexpr (sizeof(K) == 4 || sizeof(K) == 8) return (K* const*)a.inst_ptrs;
+        return nullptr;
+    }
+
     static Inst inst_of(const PlanK& pl, const SortArgs& a)
     {
         Inst in;
@@ -366,7 +373,7 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
         if (e != cudaSuccess) return e;
         const int64_t grid = pl.n_inst * pl.n_B * pl.R0;
         ProfScope ps_("tile_sort", s);
-        f<<<(unsigned)grid, TNT, tile_smem(), s>>>(src, dst, inst_of(pl, a_), pl.n_B, pl.R0);
+        f<<<(unsigned)grid, TNT, tile_smem(), s>>>(src, dst, inst_of(pl, a_), pl.n_B, pl.R0, iptrs(a_));
         return cudaGetLastError();
     }
 
@@ -376,9 +383,10 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
     // variant: ps_merge_variant of the last level's chunk merge.
     template <int XF>
     // G0: groups of the job (default: the shape's capacity, every group).
+    // own: write the output to the instances' own buffers (SortArgs::inst_ptrs).
     static cudaError_t merge(const MergeJob& job, const MergeShape& sh, GBuf<K> src, GBuf<K> dst,
                              const PlanK& pl, char* ws, cudaStream_t s, int variant = PS_MERGE_TREE,
-                             int64_t G0 = -1)
+                             int64_t G0 = -1, K* const* own = nullptr)
     {
         if (G0 < 0) G0 = sh.G[0];
         const bool fin = job.kind == 1;
@@ -431,6 +439,7 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
         const Level& Lf = Lv[sh.nlev];
         const int64_t gf = sh.G[sh.nlev];
         if (variant == PS_MERGE_SELECT) {
+            if (own) return cudaErrorInvalidValue;  // the selection tree writes dst only
             // one thread per group, each with its own selection tree
             int KP = 1;
             while (KP < Kr) KP <<= 1;
@@ -448,14 +457,14 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
         if ((e = smem_attr(fm, merge_smem(Kr))) != cudaSuccess) return e;
         {
             ProfScope ps_(fin ? "merge_final" : "merge_inblock", s);
-            fm<<<(unsigned)gf, MNT, merge_smem(Kr), s>>>(Lf, src, dst, pl.N, big + 1, nbig);
+            fm<<<(unsigned)gf, MNT, merge_smem(Kr), s>>>(Lf, src, dst, pl.N, big + 1, nbig, own, job.in);
         }
         auto fb = k_merge<MNT, BE, K, XF, true, false>;
         if ((e = smem_attr(fb, big_smem(Kr))) != cudaSuccess) return e;
         {
             ProfScope ps_(fin ? "merge_big_final" : "merge_big_inblock", s);
             fb<<<(unsigned)std::min<int64_t>(gf, 2 * 152), MNT, big_smem(Kr), s>>>(Lf, src, dst, pl.N, big + 1,
-                                                                                    nbig);
+                                                                                    nbig, own, job.in);
         }
         return cudaGetLastError();
     }
@@ -493,7 +502,9 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
             GBuf<K> nxt = same_buf(cur, wsb) ? user : wsb;
             if (p + 1 == pl.npass && end_in_user) nxt = last;
             if (p + 1 == pl.npass && end_in_user && !a.keep_order_keys) {
-                if ((e = merge<XF>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) return e;
+                if ((e = merge<XF>(job, pl.inblock[p], cur, nxt, pl, ws, s, PS_MERGE_TREE, -1, iptrs(a))) !=
+                    cudaSuccess)
+                    return e;
             } else if ((e = merge<0>(job, pl.inblock[p], cur, nxt, pl, ws, s)) != cudaSuccess) {
                 return e;
             }
@@ -581,7 +592,8 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done, 0);
             cudaEventDestroy(done);
             if (e != cudaSuccess) return e;
-        } else if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, last, pl, ws, s, a.merge_variant)) != cudaSuccess) {
+        } else if (!pl.direct && (e = merge<XF>(job, pl.fin, cur, last, pl, ws, s, a.merge_variant, -1, iptrs(a))) !=
+                                     cudaSuccess) {
             return e;
         }
         // Trace (single sorts only).
@@ -648,7 +660,7 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
         in.n0 = a.n_max;
         GBuf<K> user = gbuf_user<K>(a);
         ProfScope ps_("small_sort", a.stream);
-        f<<<(unsigned)a.n_inst, SNT, sm, a.stream>>>(user, user, in, 1, 1);
+        f<<<(unsigned)a.n_inst, SNT, sm, a.stream>>>(user, user, in, 1, 1, iptrs(a));
         return cudaGetLastError();
     }
 

@@ -5,9 +5,10 @@
 // One worker thread owns the device work.  Submitted requests wait in a FIFO
 // queue; whenever a stream slot is free and the in-flight limit and the memory
 // budget allow, the worker admits the queue's head requests as one round,
-// gathers each (dtype, pivot mode) group of the round into one staging buffer,
-// sorts it with the batched pipeline (every request a segment), scatters the
-// results back, and queues a host callback that retires the round.  Rounds run
+// sorts each (dtype, pivot mode) group of the round with the batched pipeline
+// in place (every request a segment read from and written back to its own
+// buffer; a scratch buffer of the group's size carries the passes in
+// between), and queues a host callback that retires the round.  Rounds run
 // on several streams, so a round admitted while earlier ones are on the GPU
 // overlaps with them.  A request's result is bit-identical to ps_sort on it
 // alone: batching changes only which launches carry it.
@@ -125,10 +126,10 @@ struct Server {
                 inject = true;
             }
         }
-        // one pinned table for the whole round (2 int64 per request); every
-        // group stages its instance table in its own part of it, and the slot
-        // reuses it only after the round has retired
-        const size_t need = 2 * r->reqs.size();
+        // one pinned table for the whole round (3 int64 per request: start,
+        // length, buffer); every group stages its instance table in its own
+        // part of it, and the slot reuses it only after the round has retired
+        const size_t need = 3 * r->reqs.size();
         if (sl.pinned_cap < need) {
             if (sl.pinned) cudaFreeHost(sl.pinned);
             sl.pinned = nullptr;
@@ -154,23 +155,14 @@ struct Server {
             for (size_t k = 0; k < grp.size(); k++) off[k + 1] = off[k] + r->reqs[grp[k]].n;
             const int64_t total = off.back();
             int64_t* pin = sl.pinned ? sl.pinned + pin_at : nullptr;
-            const size_t pin_cap = sl.pinned ? 2 * grp.size() : 0;
-            pin_at += 2 * grp.size();
-            void* stage = nullptr;
+            const size_t pin_cap = sl.pinned ? 3 * grp.size() : 0;
+            pin_at += 3 * grp.size();
+            std::vector<void*> own(grp.size());
+            for (size_t k = 0; k < grp.size(); k++) own[k] = r->reqs[grp[k]].keys;
+            void* stage = nullptr;  // the passes between the first and the last
             rc = ws_alloc(&stage, (size_t)total * kb, st);
             if (rc != PS_OK) break;
-            cudaError_t e = cudaSuccess;
-            for (size_t k = 0; k < grp.size() && e == cudaSuccess; k++) {
-                const Req& q = r->reqs[grp[k]];
-                e = cudaMemcpyAsync((char*)stage + off[k] * kb, q.keys, (size_t)q.n * kb, cudaMemcpyDeviceToDevice, st);
-            }
-            if (e == cudaSuccess) rc = batch_sort(off, stage, dtype, mode, st, pin, pin_cap);
-            else rc = fail_cuda(e);
-            for (size_t k = 0; k < grp.size() && rc == PS_OK; k++) {
-                const Req& q = r->reqs[grp[k]];
-                e = cudaMemcpyAsync(q.keys, (char*)stage + off[k] * kb, (size_t)q.n * kb, cudaMemcpyDeviceToDevice, st);
-                if (e != cudaSuccess) rc = fail_cuda(e);
-            }
+            rc = batch_sort(off, stage, dtype, mode, st, pin, pin_cap, nullptr, &own);
             ws_free(stage, st);
         }
         r->status = rc;
