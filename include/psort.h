@@ -245,11 +245,13 @@ int ps_last_cuda_error(void);
  * A server sorts device buffers submitted from any host thread.  Requests
  * queue in arrival order; a worker thread admits the queue's head whenever a
  * stream slot is free, fewer than max_inflight requests are on the GPU and the
- * memory budget holds the request's cost (a staging copy of its keys plus the
- * sort's workspace).  Each admission round is gathered into one batched sort
- * per (dtype, pivot mode), run on one of several server streams, so rounds
- * admitted while others run overlap on the GPU.  Results are bit-identical to
- * ps_sort on each buffer alone.
+ * memory budget holds the request's cost (scratch for a copy of its keys plus
+ * the sort's workspace).  Each admission round runs as one batched sort per
+ * (dtype, pivot mode) that reads every request from its own buffer and writes
+ * the result back there (no gather or scatter copies), on one of several
+ * server streams, so rounds admitted while others run overlap on the GPU.
+ * Results are bit-identical to ps_sort on each buffer alone.  A round that
+ * fails on the device may leave its requests' keys partly rewritten.
  *   ps_server_open    budget in bytes (> 0), max_inflight >= 1; the server
  *                     uses the device current at open.
  *   ps_server_submit  dev_keys must hold the n keys when submitted (ordered
