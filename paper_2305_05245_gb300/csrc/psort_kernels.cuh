@@ -23,6 +23,12 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Registers a record (uint64 key + uint32 payload) counts for when a data
+// kernel's CTAs per SM are chosen (data_ctas below).
+#ifndef PS_REC_REGW
+#define PS_REC_REGW 3
+#endif
+
 namespace ps {
 
 // ----------------------------------------------------------- checked builds
@@ -218,7 +224,7 @@ template <typename K, int E> struct TileBuf {
     using type = SBuf<K, TilePad<K, E>::v>;
 };
 
-// ------------------------------------------- asynchronous global->shared copies// ------------------------------------------- asynchronous global->shared copies
+// ------------------------------------------- asynchronous global->shared copies
 // cp.async (Ampere-and-later LDGSTS): each thread queues element copies
 // without staging them in registers, so a CTA keeps many loads in flight.
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
@@ -403,6 +409,7 @@ __device__ __forceinline__ uint64_t shfl_key(uint64_t v, int m)
     const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, (uint32_t)(v >> 32), m);
     return ((uint64_t)hi << 32) | lo;
 }
+__device__ __forceinline__ Rec shfl_key(const Rec& v, int m) { return Rec{shfl_key(v.k, m), shfl_key(v.p, m)}; }
 // The lower lane of a compare pair keeps the smaller key, the upper lane the
 // larger one (equal keys are identical bit patterns, so either may stay).
 template <typename K> __device__ __forceinline__ K keep(const K& mine, const K& other, bool upper)
@@ -740,7 +747,7 @@ __device__ __forceinline__ void block_bounds(int64_t N, int64_t n_B, int64_t b, 
 // more than 1024 threads per SM in all.
 template <typename K, int NT, int E> constexpr int data_ctas()
 {
-    constexpr int w = sizeof(K) == 4 ? 1 : sizeof(K) == 8 ? 2 : 3;
+    constexpr int w = sizeof(K) == 4 ? 1 : sizeof(K) == 8 ? 2 : PS_REC_REGW;
     constexpr int c = 65536 / (NT * (16 + w * E));
     constexpr int cap = 1024 / NT < 1 ? 1 : 1024 / NT;
     return c < 1 ? 1 : (c > cap ? cap : c);
@@ -791,17 +798,49 @@ __device__ __forceinline__ void tile_load_regs(const GBuf<K>& src, int64_t o, in
             }
     }
 }
+// Records: the same positions, two records per step (a 16-byte vector of
+// keys and an 8-byte vector of payloads from the two arrays).
+template <int NT, int E, typename K, int XF>
+__device__ __forceinline__ void tile_load_regs(const GBuf<Rec>& src, int64_t o, int n, Rec (&r)[E])
+{
+    static_assert(E % 2 == 0, "records per thread must be even");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = w * 32 * E + lane * 2;
+    const uint64_t* gk = src.k + o;
+    const uint32_t* gp = src.p + o;
+    if (n == NT * E && ((uintptr_t)gk & 15) == 0 && ((uintptr_t)gp & 7) == 0) {
+#pragma unroll
+        for (int v = 0; v < E / 2; v++) {
+            const int i = base + v * 64;
+            ulonglong2 x = make_ulonglong2(0, 0);
+            uint2 y = make_uint2(0, 0);
+            if (PS_IN(o + i + 1, src.n, 3)) {
+                x = __ldcs((const ulonglong2*)(gk + i));
+                y = __ldcs((const uint2*)(gp + i));
+            }
+            r[v * 2] = Rec{x.x, y.x};
+            r[v * 2 + 1] = Rec{x.y, y.y};
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < E / 2; v++)
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int i = base + v * 64 + q;
+                r[v * 2 + q] = i < n ? src.ld(o + i) : KT<Rec>::maxkey();
+            }
+    }
+}
 
 // One CTA sorts one tile of NT*E keys of one block of one instance (tiles
 // never straddle a block boundary; every block gets R0 tile slots, the
 // number the longest block needs).  Loads apply the order-key transform XF.
 // Missing keys of a short tile count as the largest key, which sorts last
 // and is never written.  FINAL: the tile is the whole sorted result, so the
-// store applies the inverse transform.  Plain keys: loads straight into
-// registers (tile_load_regs), a register sorting network per thread, WLEV
-// warp-shuffle merge levels, then shared-memory merge-path levels for the
-// rest.  Records: cp.async staging through shared memory, then the same
-// network and shared-memory levels.
+// store applies the inverse transform.  Loads go straight into registers
+// (tile_load_regs), then a register sorting network per thread, WLEV
+// warp-shuffle merge levels, and shared-memory merge-path levels for the
+// rest.
 // iptr (plain keys, batches): instance i's keys live in their own buffer
 // iptr[i] (in the compact layout they would start at in.off(i)); the tile is
 // read from there and, when FINAL, written back there.
@@ -811,7 +850,6 @@ __global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
 {
     constexpr int T = NT * E;
     constexpr bool PLAIN = sizeof(K) == 4 || sizeof(K) == 8;
-    static_assert(PLAIN || WLEV == 0, "records take no shuffle levels");
     using SB = typename TileBuf<K, E>::type;
     using SV = typename ViewOf<SB>::type;
     extern __shared__ __align__(16) char smem[];
@@ -837,15 +875,7 @@ __global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
             tile_load_regs<NT, E, K, XF>(src, o, n, r);
         }
     } else {
-        for (int i = threadIdx.x; i < n; i += NT) cp_elem(sb, i, src, o + i);
-        cp_async_wait_all();
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-            const int i = threadIdx.x * E + j;
-            r[j] = i < n ? xform<XF>(sb.ld(i)) : KT<K>::maxkey();
-        }
-        __syncthreads();
+        tile_load_regs<NT, E, K, XF>(src, o, n, r);
     }
     reg_sort<E>(r);
     if constexpr (WLEV > 0) warp_merge_levels<E, WLEV>(r);

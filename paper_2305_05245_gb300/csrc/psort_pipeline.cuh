@@ -18,12 +18,15 @@ namespace ps {
 // the chunk capacity) and of the sample pool (PNT, PE; PNT*PE samples).
 // Shuffle levels measured on GB300 (2^30 keys): 64-bit keys 2 (a shuffle
 // level's compare-exchanges cost more ALU work than a shared-memory level
-// beyond that), 32-bit keys 5 (all levels inside a warp).
+// beyond that), 32-bit keys 5 (all levels inside a warp); records (2^28) 1.
 #ifndef PS_TILE_WLEV32
 #define PS_TILE_WLEV32 5
 #endif
 #ifndef PS_TILE_WLEV64
 #define PS_TILE_WLEV64 2
+#endif
+#ifndef PS_TILE_WLEVREC
+#define PS_TILE_WLEVREC 1
 #endif
 // Target chunk size of a merge, in percent of the room a chunk has after the
 // average padding (splitters land within a few percent of their targets;
@@ -47,7 +50,7 @@ template <> struct Cfg<uint64_t> {
     static constexpr int TNT = 256, TE = 32, TW = PS_TILE_WLEV64, MNT = 256, ME = 32, PNT = 1024, PE = 8;
 };
 template <> struct Cfg<Rec> {
-    static constexpr int TNT = 256, TE = 16, TW = 0, MNT = 256, ME = 16, PNT = 512, PE = 8;
+    static constexpr int TNT = 256, TE = 16, TW = PS_TILE_WLEVREC, MNT = 256, ME = 16, PNT = 512, PE = 8;
 };
 
 constexpr int64_t FMAX = 256;  // largest fan-in of one in-block merge pass

@@ -150,7 +150,8 @@ def test_parity_shapes(ps, ora, n, dtype, dist, n_B, n_P, mode):
 
 @pytest.mark.parametrize("mode", ["regular", "exact"])
 @pytest.mark.parametrize("n,dist,n_B,n_P", [(1000, "uniform", 3, 4), (100_003, "few_unique", 8, 8),
-                                              (250_000, "uniform", 1, 64), (70_001, "sorted", 64, 5)])
+                                              (250_000, "uniform", 1, 64), (70_001, "sorted", 64, 5),
+                                              (262_221, "few_unique", 2, 16)])
 def test_parity_records(ps, ora, n, dist, n_B, n_P, mode):
     k, p = synth.records(n, seed=synth.seed_for("rec", n, dist), dist=dist)
     out, pay, t = run_gpu(ps, k, mode, n_B, n_P, payload=p)
