@@ -164,11 +164,13 @@ int ps_sort_struct(void* records, int64_t n, int64_t record_bytes, int64_t key_o
 
 /* Sort many independent segments of one key array in place: segment i is
  * keys[seg_offsets[i], seg_offsets[i+1]) (seg_offsets: n_segs+1 non-decreasing
- * DEVICE int64 offsets).  Segments are binned by length; every bin runs the
- * four-step method on all of its segments at once (segments that fit one
- * shared-memory tile are sorted by one CTA each, in a single launch), so the
- * number of kernel launches depends on the number of size bins, not on the
- * number of segments.  Each segment's result equals ps_sort on it alone.
+ * DEVICE int64 offsets).  Segments are binned by length.  Every segment of at
+ * most one shared-memory tile (8192 keys) is sorted by one persistent launch
+ * (a grid sized to the GPU whose CTAs take work items from a device counter:
+ * a CTA per segment above 1024 keys, a warp per segment up to 1024 keys);
+ * every longer bin runs the four-step method on all of its segments at once.
+ * So the number of kernel launches depends on the number of size bins, not
+ * on the number of segments.  Each segment's result equals ps_sort on it alone.
  * The call reads seg_offsets back to the host (it waits for `stream` once,
  * before queuing the sort); it returns once the sort is queued. */
 int ps_sort_batch(const int64_t* seg_offsets, int64_t n_segs, void* keys, int dtype, int pivot_mode,

@@ -375,14 +375,16 @@ size_t sort_ws_bytes(int64_t n, int dtype)
 
 // Batched sorts.  A batch plan bins the segments [off[i], off[i+1]) by length
 // and fixes each bin's parameters and its part of the instance table (per
-// bin: all starts, then all lengths); launching a plan queues one
-// multi-instance pipeline per bin.
+// bin: all starts, then all lengths); launching a plan queues one persistent
+// launch for the segments of at most one tile (both short bins together) and
+// one multi-instance pipeline per longer bin.
 struct BatchBin {
     size_t at;                // offset of the bin's starts in the instance table
     int64_t cnt, nmax, nsum;  // instances, longest, total keys
     int64_t n_B, n_P;
     int items, threads;       // launch shape (0, 0: automatic)
-    bool small;               // at most SMALL_SEG keys each: one small CTA per segment
+    bool small;               // at most SMALL_SEG keys each (one warp each)
+    bool front;               // at most one tile each: sorted by the persistent front kernel
 };
 struct BatchPlan {
     int dtype = 0, mode = 0;
@@ -390,6 +392,7 @@ struct BatchPlan {
     bool own = false;            // segments in buffers of their own (per bin: starts, lengths, pointers)
     std::vector<int64_t> table;  // host copy of the instance table
     std::vector<BatchBin> bins;
+    size_t counter_at = 0;       // the front kernel's work counter (last table slot), if a front bin exists
 };
 
 // own (optional): one device pointer per segment; segment i then lives in its
@@ -409,8 +412,8 @@ static int batch_make_plan(const std::vector<int64_t>& off, int dtype, int mode,
     if (own && own->size() < (size_t)n_segs) return PS_ERR_INVALID_ARG;
     bp->table.clear();
     bp->bins.clear();
-    // bins: 0 = at most SMALL_SEG keys (one small CTA each); 1 = fits one
-    // tile (one tile-sort CTA each); b >= 2 = lengths in (T*2^(b-2), T*2^(b-1)]
+    // bins: 0 = at most SMALL_SEG keys (a warp each); 1 = fits one tile (a
+    // CTA each); b >= 2 = lengths in (T*2^(b-2), T*2^(b-1)]
     const int64_t tile = 8192;
     std::vector<std::vector<int64_t>> bins(48);
     for (int64_t i = 0; i < n_segs; i++) {
@@ -450,8 +453,15 @@ static int batch_make_plan(const std::vector<int64_t>& off, int dtype, int mode,
         bb.items = b <= 1 ? 0 : r.items_per_thread;
         bb.threads = b <= 1 ? 0 : r.block_threads;
         bb.small = b == 0;
+        bb.front = b <= 1;
         bp->bins.push_back(bb);
     }
+    for (const BatchBin& bb : bp->bins)
+        if (bb.front) {
+            bp->counter_at = bp->table.size();
+            bp->table.push_back(0);
+            break;
+        }
     return PS_OK;
 }
 
@@ -482,19 +492,37 @@ static SortArgs batch_bin_args(const BatchPlan& bp, const BatchBin& bb, const in
 
 static bool narrow_dtype(int dtype) { return dtype == PS_I32 || dtype == PS_F32 || dtype == PS_U32; }
 
-// Queue every bin of a plan on s.  ws == nullptr: each bin takes its
-// workspace from the pool; otherwise every bin runs on ws (cap bytes) and
+// Queue every bin of a plan on s: the short bins in one persistent launch,
+// then one pipeline per longer bin.  ws == nullptr: each pipeline takes its
+// workspace from the pool; otherwise every one runs on ws (cap bytes) and
 // nothing is allocated.
 static int batch_launch(const BatchPlan& bp, const int64_t* dev_table, void* keys, cudaStream_t s, char* ws,
                         size_t cap)
 {
     const bool narrow = narrow_dtype(bp.dtype);
     int rc = PS_OK;
+    SortArgs ft, fs;
+    const SortArgs *pt = nullptr, *psm = nullptr;
+    for (const BatchBin& bb : bp.bins) {
+        if (!bb.front) continue;
+        if (bb.small) {
+            fs = batch_bin_args(bp, bb, dev_table, keys, s);
+            psm = &fs;
+        } else {
+            ft = batch_bin_args(bp, bb, dev_table, keys, s);
+            pt = &ft;
+        }
+    }
+    if (pt || psm) {
+        // the counter is a slot of the device instance table, which the
+        // plan owns (const only as the table's view)
+        unsigned long long* next = (unsigned long long*)const_cast<int64_t*>(dev_table + bp.counter_at);
+        rc = narrow ? run_front_u32(pt, psm, next) : run_front_u64(pt, psm, next);
+    }
     for (size_t i = 0; i < bp.bins.size() && rc == PS_OK; i++) {
+        if (bp.bins[i].front) continue;
         SortArgs a = batch_bin_args(bp, bp.bins[i], dev_table, keys, s);
-        if (bp.bins[i].small) {
-            rc = narrow ? run_small_u32(a) : run_small_u64(a);
-        } else if (ws) {
+        if (ws) {
             const ShapeEntry* sh = shape_of(a.dtype, a.items, a.threads, &rc);
             if (rc == PS_OK)
                 rc = sh ? sh->run_on(a, ws, cap) : narrow ? run_sort_u32_on(a, ws, cap) : run_sort_u64_on(a, ws, cap);
@@ -884,7 +912,7 @@ int ps_batch_plan_create(const int64_t* host_seg_offsets, int64_t n_segs, int dt
     int rc = batch_make_plan(off, dtype, pivot_mode, nullptr, &p->plan);
     size_t ws = 0;
     for (const BatchBin& bb : p->plan.bins) {
-        if (bb.small) continue;
+        if (bb.front) continue;
         SortArgs a = batch_bin_args(p->plan, bb, nullptr, nullptr, nullptr);
         int src = PS_OK;
         const ShapeEntry* sh = shape_of(dtype, a.items, a.threads, &src);

@@ -117,9 +117,11 @@ size_t sort_ws_bytes(int64_t n, int dtype);
 // The same sorts on a caller-provided workspace (allocation-free entry point).
 int run_sort_u32_on(const SortArgs& a, char* ws, size_t cap);
 int run_sort_u64_on(const SortArgs& a, char* ws, size_t cap);
-// Batches of instances of at most 1024 keys each: one small CTA per instance.
-int run_small_u32(const SortArgs& a);
-int run_small_u64(const SortArgs& a);
+// The short instances of a batch in one persistent launch: t (optional)
+// instances of at most one tile, sm (optional) instances of at most
+// SMALL_SEG keys; next: a device counter the call zeroes on the stream.
+int run_front_u32(const SortArgs* t, const SortArgs* sm, unsigned long long* next);
+int run_front_u64(const SortArgs* t, const SortArgs* sm, unsigned long long* next);
 constexpr int64_t SMALL_SEG = 1024;
 // Workspace bytes of the sort a describes (batched instances included).
 size_t ws_bytes_args_u32(const SortArgs& a);

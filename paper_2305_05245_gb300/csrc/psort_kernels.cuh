@@ -832,15 +832,37 @@ __device__ __forceinline__ void tile_load_regs(const GBuf<Rec>& src, int64_t o, 
     }
 }
 
+// One tile of n <= NT*E keys, read from src at so and written to dst at dso
+// (FINAL: with the inverse transform): loads straight into registers
+// (tile_load_regs), a register sorting network per thread, WLEV warp-shuffle
+// merge levels, then shared-memory merge-path levels for the rest.  Missing
+// keys of a short tile count as the largest key, which sorts last and is
+// never written.  The final loop still reads sb: a caller that reuses sb
+// synchronises the CTA first.
+template <int NT, int E, typename K, int XF, bool FINAL, int WLEV, typename SB>
+__device__ __forceinline__ void tile_sort_body(const SB& sb, const GBuf<K>& src, int64_t so, const GBuf<K>& dst,
+                                               int64_t dso, int n)
+{
+    constexpr int T = NT * E;
+    using SV = typename ViewOf<SB>::type;
+    K r[E];
+    tile_load_regs<NT, E, K, XF>(src, so, n, r);
+    reg_sort<E>(r);
+    if constexpr (WLEV > 0) warp_merge_levels<E, WLEV>(r);
+    store_bitonic<E>(SV{sb}, threadIdx.x * E, E << WLEV, (E << WLEV) >= T, r);
+    __syncthreads();
+    merge_levels_pow2<NT, E>(SV{sb}, E << (WLEV + 1));
+    for (int i = threadIdx.x; i < n; i += NT) {
+        if (FINAL) dst.template stx<XF>(dso + i, sb.ld(i));
+        else dst.st(dso + i, sb.ld(i));
+    }
+}
+
 // One CTA sorts one tile of NT*E keys of one block of one instance (tiles
 // never straddle a block boundary; every block gets R0 tile slots, the
 // number the longest block needs).  Loads apply the order-key transform XF.
-// Missing keys of a short tile count as the largest key, which sorts last
-// and is never written.  FINAL: the tile is the whole sorted result, so the
-// store applies the inverse transform.  Loads go straight into registers
-// (tile_load_regs), then a register sorting network per thread, WLEV
-// warp-shuffle merge levels, and shared-memory merge-path levels for the
-// rest.
+// FINAL: the tile is the whole sorted result, so the store applies the
+// inverse transform.
 // iptr (plain keys, batches): instance i's keys live in their own buffer
 // iptr[i] (in the compact layout they would start at in.off(i)); the tile is
 // read from there and, when FINAL, written back there.
@@ -851,7 +873,6 @@ __global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
     constexpr int T = NT * E;
     constexpr bool PLAIN = sizeof(K) == 4 || sizeof(K) == 8;
     using SB = typename TileBuf<K, E>::type;
-    using SV = typename ViewOf<SB>::type;
     extern __shared__ __align__(16) char smem[];
     char* sp = smem;
     SB sb = SB::carve(sp, T);
@@ -866,32 +887,80 @@ __global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
     if (ts >= be) return;
     const int64_t o = in.off(inst) + ts;
     const int n = (int)(be - ts < T ? be - ts : T);
-    K r[E];
     if constexpr (PLAIN) {
         if (iptr) {
             const GBuf<K> own{iptr[inst] + ts, (int64_t)n};
-            tile_load_regs<NT, E, K, XF>(own, 0, n, r);
-        } else {
-            tile_load_regs<NT, E, K, XF>(src, o, n, r);
-        }
-    } else {
-        tile_load_regs<NT, E, K, XF>(src, o, n, r);
-    }
-    reg_sort<E>(r);
-    if constexpr (WLEV > 0) warp_merge_levels<E, WLEV>(r);
-    store_bitonic<E>(SV{sb}, threadIdx.x * E, E << WLEV, (E << WLEV) >= T, r);
-    __syncthreads();
-    merge_levels_pow2<NT, E>(SV{sb}, E << (WLEV + 1));
-    if constexpr (PLAIN && FINAL) {
-        if (iptr) {
-            const GBuf<K> own{iptr[inst] + ts, (int64_t)n};
-            for (int i = threadIdx.x; i < n; i += NT) own.template stx<XF>(i, sb.ld(i));
+            if (FINAL) tile_sort_body<NT, E, K, XF, FINAL, WLEV>(sb, own, 0, own, 0, n);
+            else tile_sort_body<NT, E, K, XF, FINAL, WLEV>(sb, own, 0, dst, o, n);
             return;
         }
     }
-    for (int i = threadIdx.x; i < n; i += NT) {
-        if (FINAL) dst.template stx<XF>(o + i, sb.ld(i));
-        else dst.st(o + i, sb.ld(i));
+    tile_sort_body<NT, E, K, XF, FINAL, WLEV>(sb, src, o, dst, o, n);
+}
+
+// ------------------------------------------- batches: persistent front kernel
+// Sorts every short instance of a batch in one launch of a grid sized to the
+// GPU (persistent CTAs).  Work items come from one device counter (*next,
+// zero at launch): items [0, tiles.count) are instances of at most NT*E keys,
+// each sorted by the whole CTA (tile_sort_body); the items after them are
+// groups of NT/32 instances of at most 1024 keys, one per warp, each sorted
+// in registers (32 keys per lane, a sorting network, then five warp-shuffle
+// merge levels: 32 runs of 32 become one run of 1024) and written out through
+// the warp's own part of shared memory.  Larger items come first, so the
+// short ones fill in behind them.  tptr/sptr (optional): each instance in
+// its own buffer, as in k_tile_sort.
+template <int NT, int E, typename K, int XF, int WLEV>
+__global__ void __launch_bounds__(NT, (data_ctas<K, NT, E>()))
+    k_batch_front(GBuf<K> keys, Inst tiles, K* const* tptr, Inst small, K* const* sptr, unsigned long long* next)
+{
+    static_assert(E == 32 && NT * E >= (NT / 32) * 1024, "one 1024-key run per warp in the tile buffer");
+    constexpr int T = NT * E;
+    constexpr int WARPS = NT / 32;
+    using SB = typename TileBuf<K, E>::type;
+    using SV = typename ViewOf<SB>::type;
+    extern __shared__ __align__(16) char smem[];
+    __shared__ unsigned long long item_s;
+    char* sp = smem;
+    SB sb = SB::carve(sp, T);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long n_groups = (small.count + WARPS - 1) / WARPS;
+    const unsigned long long total = (unsigned long long)(tiles.count + n_groups);
+    for (;;) {
+        // thread 0 writes item_s again only after the barrier that ends the
+        // item, which every thread reaches after reading it
+        if (threadIdx.x == 0) item_s = atomicAdd(next, 1ull);
+        __syncthreads();
+        const unsigned long long item = item_s;
+        if (item >= total) return;
+        if (item < (unsigned long long)tiles.count) {
+            const int64_t i = (int64_t)item;
+            const int n = (int)tiles.len(i);
+            if (tptr) {
+                const GBuf<K> own{tptr[i], (int64_t)n};
+                tile_sort_body<NT, E, K, XF, true, WLEV>(sb, own, 0, own, 0, n);
+            } else {
+                tile_sort_body<NT, E, K, XF, true, WLEV>(sb, keys, tiles.off(i), keys, tiles.off(i), n);
+            }
+        } else {
+            const int64_t i = (int64_t)(item - (unsigned long long)tiles.count) * WARPS + w;
+            if (i < small.count) {
+                const int n = (int)small.len(i);
+                const GBuf<K> g = sptr ? GBuf<K>{sptr[i], (int64_t)n} : keys;
+                const int64_t o = sptr ? 0 : small.off(i);
+                K r[E];
+#pragma unroll
+                for (int j = 0; j < E; j++) {
+                    const int x = j * 32 + lane;  // coalesced; which keys a lane holds does not matter
+                    r[j] = x < n ? xform<XF>(g.ld(o + x)) : KT<K>::maxkey();
+                }
+                reg_sort<E>(r);
+                warp_merge_levels<E, 5>(r);  // lane l now holds positions l*32 .. l*32+31
+                store_block<E>(SV{sb}, w * 1024 + lane * E, r);
+                __syncwarp();
+                for (int x = lane; x < n; x += 32) g.template stx<XF>(o + x, sb.ld(w * 1024 + x));
+            }
+        }
+        __syncthreads();  // the tile buffer is free again
     }
 }
 

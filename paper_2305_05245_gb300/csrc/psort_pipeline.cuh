@@ -636,34 +636,53 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
             pl.make(a.n, 1, a.n, a.n, a.n_B, a.n_P, a.mode);
     }
 
-    // Small instances (every one at most SNT * SE keys, n_B = n_P = 1): one
-    // small CTA sorts each instance in shared memory and writes the result.
-    static constexpr int SNT = 64, SE = 16;
-    static int run_small(const SortArgs& a)
+    // The short instances of a batch in one persistent launch
+    // (k_batch_front): t (optional) holds instances of at most one tile,
+    // sm (optional) instances of at most 1024 keys; *next is zeroed here on
+    // the stream before the launch.  Both argument sets share the keys
+    // buffer, the dtype and, when set, the own-buffer pointers.
+    static int run_front(const SortArgs* t, const SortArgs* sm, unsigned long long* next)
     {
+        const SortArgs& a = t ? *t : *sm;
         cudaError_t e;
         switch (xf_of(a.dtype)) {
-        case 1: e = small_xf<1>(a); break;
-        case 2: e = small_xf<2>(a); break;
-        default: e = small_xf<0>(a); break;
+        case 1: e = front_xf<1>(t, sm, next); break;
+        case 2: e = front_xf<2>(t, sm, next); break;
+        default: e = front_xf<0>(t, sm, next); break;
         }
         return e == cudaSuccess ? PS_OK : fail_cuda(e);
     }
-    template <int XF> static cudaError_t small_xf(const SortArgs& a)
+    template <int XF> static cudaError_t front_xf(const SortArgs* t, const SortArgs* sm, unsigned long long* next)
     {
-        if (a.n_max > SNT * SE) return cudaErrorInvalidValue;
-        auto f = k_tile_sort<SNT, SE, K, XF, true, C::TW>;
-        const size_t sm = TileBuf<K, SE>::type::bytes(SNT * SE) + 64;
-        cudaError_t e = smem_attr(f, sm);
+        constexpr int NT = C::TNT, E = C::TE;
+        const SortArgs& a = t ? *t : *sm;
+        if ((t && t->n_max > NT * E) || (sm && sm->n_max > (int64_t)SMALL_SEG)) return cudaErrorInvalidValue;
+        auto f = k_batch_front<NT, E, K, XF, C::TW>;
+        const size_t smb = TileBuf<K, E>::type::bytes(NT * E) + 64;
+        cudaError_t e = smem_attr(f, smb);
         if (e != cudaSuccess) return e;
-        Inst in;
-        in.base = a.inst_base;
-        in.n = a.inst_n;
-        in.count = a.n_inst;
-        in.n0 = a.n_max;
+        auto inst_of = [](const SortArgs* x) {
+            Inst in;
+            in.base = x ? x->inst_base : nullptr;
+            in.n = x ? x->inst_n : nullptr;
+            in.count = x ? x->n_inst : 0;
+            in.n0 = 0;
+            return in;
+        };
+        const Inst ti = inst_of(t), si = inst_of(sm);
+        const int64_t items = ti.count + (si.count + NT / 32 - 1) / (NT / 32);
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, NT, smb);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * std::max(per_sm, 1)));
+        e = cudaMemsetAsync(next, 0, sizeof(*next), a.stream);
+        if (e != cudaSuccess) return e;
         GBuf<K> user = gbuf_user<K>(a);
-        ProfScope ps_("small_sort", a.stream);
-        f<<<(unsigned)a.n_inst, SNT, sm, a.stream>>>(user, user, in, 1, 1, iptrs(a));
+        ProfScope ps_("batch_front", a.stream);
+        f<<<(unsigned)grid, NT, smb, a.stream>>>(user, ti, t ? iptrs(*t) : nullptr, si, sm ? iptrs(*sm) : nullptr,
+                                                 next);
         return cudaGetLastError();
     }
 

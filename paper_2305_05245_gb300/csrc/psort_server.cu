@@ -127,9 +127,10 @@ struct Server {
             }
         }
         // one pinned table for the whole round (3 int64 per request: start,
-        // length, buffer); every group stages its instance table in its own
-        // part of it, and the slot reuses it only after the round has retired
-        const size_t need = 3 * r->reqs.size();
+        // length, buffer; plus one counter slot per group, at most one per
+        // request); every group stages its instance table in its own part of
+        // it, and the slot reuses it only after the round has retired
+        const size_t need = 4 * r->reqs.size();
         if (sl.pinned_cap < need) {
             if (sl.pinned) cudaFreeHost(sl.pinned);
             sl.pinned = nullptr;
@@ -155,8 +156,8 @@ struct Server {
             for (size_t k = 0; k < grp.size(); k++) off[k + 1] = off[k] + r->reqs[grp[k]].n;
             const int64_t total = off.back();
             int64_t* pin = sl.pinned ? sl.pinned + pin_at : nullptr;
-            const size_t pin_cap = sl.pinned ? 3 * grp.size() : 0;
-            pin_at += 3 * grp.size();
+            const size_t pin_cap = sl.pinned ? 3 * grp.size() + 1 : 0;
+            pin_at += 3 * grp.size() + 1;
             std::vector<void*> own(grp.size());
             for (size_t k = 0; k < grp.size(); k++) own[k] = r->reqs[grp[k]].keys;
             void* stage = nullptr;  // the passes between the first and the last

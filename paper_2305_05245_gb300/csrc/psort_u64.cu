@@ -5,7 +5,10 @@ namespace ps {
 int run_sort_u64(const SortArgs& a) { return Pipeline<uint64_t>::run(a); }
 size_t ws_bytes_u64(int64_t n, int64_t n_B, int64_t n_P) { return Pipeline<uint64_t>::ws_bytes(n, n_B, n_P); }
 int run_sort_u64_on(const SortArgs& a, char* ws, size_t cap) { return Pipeline<uint64_t>::run_on(a, ws, cap); }
-int run_small_u64(const SortArgs& a) { return Pipeline<uint64_t>::run_small(a); }
+int run_front_u64(const SortArgs* t, const SortArgs* sm, unsigned long long* next)
+{
+    return Pipeline<uint64_t>::run_front(t, sm, next);
+}
 size_t ws_bytes_args_u64(const SortArgs& a) { return Pipeline<uint64_t>::ws_bytes_for(a); }
 // First recorded index violation of this family's kernels (checked builds);
 // clears the record.  Returns 1 if one was recorded, 0 if none.

@@ -44,6 +44,8 @@ def to_dev(a):
     import torch
     if a.dtype == np.uint32:
         return torch.from_numpy(a.view(np.int32).copy()).cuda()
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64).copy()).cuda()
     return torch.from_numpy(a.copy()).cuda()
 
 
@@ -90,8 +92,9 @@ def test_batch_equals_per_segment_sort(ps):
 
 @pytest.mark.parametrize("dtype", ["int32", "float64"])
 def test_batch_many_tiny_segments(ps, ora, dtype):
-    """100,000 segments of 2..64 keys (the small-segment bin: one small CTA
-    per segment) plus a few at the bin edges."""
+    """100,000 segments of 2..64 keys (the small-segment bin: a warp per
+    segment in the persistent front kernel, many work items per CTA) plus a
+    few at the bin edges."""
     import torch
     z = synth.splitmix64(synth.seed_for("tiny", dtype), 100_000)
     lens = (2 + (z % np.uint64(63))).astype(np.int64)
@@ -103,6 +106,61 @@ def test_batch_many_tiny_segments(ps, ora, dtype):
     ps.sort_batch(x, torch.from_numpy(offs).cuda(), "exact")
     torch.cuda.synchronize()
     assert x.cpu().numpy().tobytes() == reference(ora, keys, offs).tobytes()
+
+
+@pytest.mark.parametrize("dtype,lens", [
+    ("int64", [1024] * 700 + [2, 3, 31, 32, 33, 1000]),          # warp items only
+    ("uint32", [8192, 1025, 4097, 2048, 7777] * 200),            # tile items only
+    ("float32", [2, 8192, 1024, 1025, 5000, 17] * 150),          # both, interleaved
+    ("uint64", [1, 0, 1024, 0, 8192, 1] * 100),                  # empty and one-key segments between
+])
+def test_batch_front_kernel(ps, ora, dtype, lens):
+    """The persistent front kernel (every segment of at most one tile): one
+    launch per batch, whatever the mix of warp and tile items, and every
+    segment equal to the oracle's plain sorted result."""
+    import ctypes
+    import torch
+    from paper_2305_05245_gb300 import _lib
+    lens = np.array(lens, dtype=np.int64)
+    offs = np.zeros(len(lens) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    dist = "gaussian" if dtype.startswith("float") else "few_unique"
+    keys = synth.keys(int(offs[-1]), dtype, dist, seed=synth.seed_for("front", dtype))
+    x = to_dev(keys)
+    o = torch.from_numpy(offs).cuda()
+    code = {"int32": 0, "int64": 1, "float32": 2, "float64": 3, "uint32": 4, "uint64": 5}[dtype]
+    lib = _lib.load()
+    ps.profile_reset()
+    ps.profile_enable(True)
+    try:
+        rc = lib.ps_sort_batch(ctypes.c_void_p(o.data_ptr()), len(lens), ctypes.c_void_p(x.data_ptr()), code, 1, None)
+        torch.cuda.synchronize()
+        prof = ps.profile_read()
+    finally:
+        ps.profile_enable(False)
+    assert rc == 0
+    assert prof.get("batch_front", (0, 0))[0] == 1, prof
+    assert set(prof) == {"batch_front"}, "segments of at most one tile take no other launch: %s" % prof
+    got = x.cpu().numpy().view(keys.dtype)
+    assert got.tobytes() == reference(ora, keys, offs).tobytes()
+
+
+def test_batch_front_float_specials(ps, ora):
+    """Signed zeros, infinities and subnormals inside warp items and tile
+    items (the order-key transform on load and its inverse on store)."""
+    import torch
+    specials = np.array([-0.0, 0.0, np.inf, -np.inf, 5e-324, -5e-324, 1.0, -1.0], dtype=np.float64)
+    lens = np.array([8, 500, 1024, 1025, 8192, 3], dtype=np.int64)
+    offs = np.zeros(len(lens) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    z = synth.splitmix64(synth.seed_for("front-specials"), int(offs[-1]))
+    keys = specials[(z % np.uint64(len(specials))).astype(np.int64)]
+    for dt in (np.float64, np.float32):
+        k = keys.astype(dt)
+        x = torch.from_numpy(k.copy()).cuda()
+        ps.sort_batch(x, torch.from_numpy(offs).cuda(), "regular")
+        torch.cuda.synchronize()
+        assert x.cpu().numpy().tobytes() == reference(ora, k, offs).tobytes()
 
 
 def test_batch_config4_shape(ps, ora):
