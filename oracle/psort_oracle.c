@@ -32,7 +32,11 @@
  *
  * Parity status: every function below is pinned by tests/test_oracle.py
  * (worked examples of Fig. 1 and Fig. 2, brute force on tiny inputs, the
- * closed form of PSES pivots, partition-membership invariants).
+ * closed form of PSES pivots, partition-membership invariants, the PSRS
+ * partition-size bound of Shi and Schaeffer).  One choice stays a reading:
+ * the paper gives no formula for the PSRS sample and pivot indices (R2), so
+ * beyond Fig. 1, Fig. 2(a) and the bound, the exact PSRS pivot values are
+ * parity unpinned.
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -643,6 +643,8 @@ template <typename K, typename CF = Cfg<K>> struct Pipeline {
     // buffer, the dtype and, when set, the own-buffer pointers.
     static int run_front(const SortArgs* t, const SortArgs* sm, unsigned long long* next)
     {
+        if (!t && !sm) return PS_OK;
+        if (!next) return PS_ERR_INVALID_ARG;
         const SortArgs& a = t ? *t : *sm;
         cudaError_t e;
         switch (xf_of(a.dtype)) {
