@@ -209,6 +209,24 @@ def oracle_time(a, n_sample: int):
     return n_sample / dt, dt, core
 
 
+# ------------------------------------------------------------ ranks (replicas)
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over all ranks of the process group (a job's time is its
+    slowest rank's); x itself without a group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank: every rank
+    is a replica that sorts the same amount of work."""
+    return world * units_per_rank / seconds
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -849,11 +867,8 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in evs]
     total_ms = sum(step_ms)
     prof = ps.profile_read()
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * a.steps / (total_ms / 1e3) / 1e9
+    total_ms = max_over_ranks(total_ms, dist, dev)
+    value = whole_job_rate(world, n * a.steps, total_ms / 1e3) / 1e9
 
     # end to end through ps_sort_host from pinned host memory
     e2e = None
@@ -863,13 +878,16 @@ def main():
         pinned.copy_(src)
         ps.sort_host(pinned, a.pivot, a.n_blocks, a.n_parts)  # warm
         times = []
+        if dist is not None:
+            dist.barrier()
         for _ in range(a.e2e_steps):
             pinned.copy_(src)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ps.sort_host(pinned, a.pivot, a.n_blocks, a.n_parts)
             times.append(time.perf_counter() - t0)
-        e2e = {"value": n * len(times) / sum(times) / 1e9, "unit": "Gkeys/s",
+        e2e_s = max_over_ranks(sum(times), dist, dev)
+        e2e = {"value": whole_job_rate(world, n * len(times), e2e_s) / 1e9, "unit": "Gkeys/s",
                "h2d_bytes_per_step": n * BYTES[a.dtype], "d2h_bytes_per_step": n * BYTES[a.dtype],
                "api": "ps_sort_host (pinned host buffer, H2D + sort + D2H + stream sync per step)"}
 
