@@ -82,9 +82,9 @@ def _sort_unsigned(ps, x, code, mode, n_B, n_P):
 def assert_parity(ora, keys, mode, n_B, n_P, out, pay, t, payload=None, check_trace=True):
     ref = ora.sort(keys, MODES[mode], n_B, n_P, payload=payload)
     if out.tobytes() != ref.out.tobytes():
-        bad = np.nonzero(out.view(np.uint8).reshape(len(out), -1).any(axis=1) !=
-                         ref.out.view(np.uint8).reshape(len(out), -1).any(axis=1))[0]
-        diff = np.nonzero(out != ref.out)[0]
+        diff = np.nonzero(out.view(np.uint8).reshape(len(out), -1) !=
+                          ref.out.view(np.uint8).reshape(len(out), -1))[0]
+        diff = np.unique(diff)
         raise AssertionError("output differs from the oracle at %d positions, first %s" %
                              (len(diff), diff[:5]))
     if payload is not None:
