@@ -19,7 +19,7 @@
 namespace ps {
 
 template <typename K, int E, int NT> struct ShapeCfg {
-    static constexpr int TNT = NT, TE = E, MNT = NT, ME = E, PNT = 1024, PE = 8;
+    static constexpr int TNT = NT, TE = E, MNT = NT, ME = E, PNT = sizeof(K) == 8 ? 512 : 1024, PE = 8;
     static constexpr int TW = sizeof(K) == 4 ? PS_TILE_WLEV32 : PS_TILE_WLEV64;
 };
 
