@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--pivot", default="exact", choices=["exact", "regular"])
     ap.add_argument("--n-blocks", type=int, default=0)
     ap.add_argument("--n-parts", type=int, default=0)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "table1", "merge_ablation", "records"])
@@ -889,7 +889,8 @@ def main():
         e2e_s = max_over_ranks(sum(times), dist, dev)
         e2e = {"value": whole_job_rate(world, n * len(times), e2e_s) / 1e9, "unit": "Gkeys/s",
                "h2d_bytes_per_step": n * BYTES[a.dtype], "d2h_bytes_per_step": n * BYTES[a.dtype],
-               "api": "ps_sort_host (pinned host buffer, H2D + sort + D2H + stream sync per step)"}
+               "api": "ps_sort_host (pinned host buffer, H2D + sort + D2H + stream sync per step)",
+               "steps": len(times), "step_ms": [round(1e3 * t, 2) for t in times]}
 
     if rank != 0:
         return 0
