@@ -616,7 +616,9 @@ def run_records(a):
                    "l2": "inputs larger than L2 (no flush needed)", "in_block_merge_passes": inblock},
         "roofline": roof,
         "sort_roofline": {"algorithmic_bytes_per_key": 48, "achieved_gbs": 48 * n / (ms / 1e3) / 1e9,
-                          "frac": 48 * n / (ms / 1e3) / 1e9 / hbm, "passes_made": 2 + inblock},
+                          "frac": 48 * n / (ms / 1e3) / 1e9 / hbm, "passes_made": 2 + inblock,
+                          "passes_gbs": (2 + inblock) * 24 * n / (ms / 1e3) / 1e9,
+                          "passes_frac": (2 + inblock) * 24 * n / (ms / 1e3) / 1e9 / hbm},
         "kernels": {kk: {"launches": v[0], "ms_per_step": v[1] / a.steps} for kk, v in prof.items()},
         "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk.summary(),
         "check": "ok" if ok else "FAILED",
@@ -929,7 +931,10 @@ def main():
         "roofline": roof,
         "sort_roofline": {"algorithmic_bytes_per_key": 4 * s, "achieved_gbs": 4 * s * n / (sort_ms / 1e3) / 1e9,
                           "frac": 4 * s * n / (sort_ms / 1e3) / 1e9 / hbm,
-                          "passes_made": 2 + inblock_passes},
+                          "passes_made": 2 + inblock_passes,
+                          # the passes actually made, each a read and a write of every key
+                          "passes_gbs": (2 + inblock_passes) * 2 * s * n / (sort_ms / 1e3) / 1e9,
+                          "passes_frac": (2 + inblock_passes) * 2 * s * n / (sort_ms / 1e3) / 1e9 / hbm},
         "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in prof.items()},
         "cpu_baseline": cpu,
         "e2e": e2e,
