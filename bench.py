@@ -916,7 +916,8 @@ def main():
     sort_ms = total_ms / a.steps
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": sort_ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": a.warmup, "ms_per_step": sort_ms, "ms_per_step_median": statistics.median(step_ms),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"int32": "i32", "int64": "int64", "float32": "f32",
                                        "float64": "f64", "uint32": "u32", "uint64": "u64"}[a.dtype],
         "data": "synthetic (SplitMix64, seeded), resident in HBM",
