@@ -18,7 +18,9 @@ namespace ps {
 // the chunk capacity) and of the sample pool (PNT, PE; PNT*PE samples).
 // Sample pools measured on GB300 (2^30 keys): 64-bit keys 512 x 8 (planning
 // 5.2 -> 4.7 ms against 1024 x 8, although it takes a third refinement level
-// in places), 32-bit keys 1024 x 8, records 512 x 8.
+// in places), 32-bit keys 1024 x 8, records 512 x 8.  Records merge chunks of
+// 512 x 16 (8192 records, 2 CTAs per SM): half the chunks of 256 x 16, so
+// planning drops from 3.3 to 2.0 ms at 2^28 for 0.6 ms more in the merges.
 // Shuffle levels measured on GB300 (2^30 keys): 64-bit keys 2 (a shuffle
 // level's compare-exchanges cost more ALU work than a shared-memory level
 // beyond that), 32-bit keys 5 (all levels inside a warp); records (2^28) 1.
@@ -53,7 +55,7 @@ template <> struct Cfg<uint64_t> {
     static constexpr int TNT = 256, TE = 32, TW = PS_TILE_WLEV64, MNT = 256, ME = 32, PNT = 512, PE = 8;
 };
 template <> struct Cfg<Rec> {
-    static constexpr int TNT = 256, TE = 16, TW = PS_TILE_WLEVREC, MNT = 256, ME = 16, PNT = 512, PE = 8;
+    static constexpr int TNT = 256, TE = 16, TW = PS_TILE_WLEVREC, MNT = 512, ME = 16, PNT = 512, PE = 8;
 };
 
 constexpr int64_t FMAX = 256;  // largest fan-in of one in-block merge pass
