@@ -824,9 +824,12 @@ static int host_pipelined(const void* host_keys, void* mapped, void* d, int64_t 
         a.presorted = true;
         rc = dispatch(a);
     }
-    if (d2) ws_free(d2, s);
     // the caller waits for s; the copy stream's work is ordered before s's
-    // sorts by the events, so both are done once s is
+    // sorts by the events, so both are done once s is.  After a failure some
+    // copy may not be ordered before s: wait for the copy stream before the
+    // buffers it may still touch go back to the pool.
+    if (sc && (e != cudaSuccess || rc != PS_OK)) cudaStreamSynchronize(sc);
+    if (d2) ws_free(d2, s);
     if (sc) cudaStreamDestroy(sc);
     for (auto& x : ev)
         if (x) cudaEventDestroy(x);
