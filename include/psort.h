@@ -195,10 +195,14 @@ int ps_batch_plan_destroy(ps_batch_plan* plan);
  * pageable; naturally aligned for the dtype): sorts them as ps_sort_ex does,
  * leaves the result in `host_keys`, and waits for `stream` to finish before
  * returning.  Page-locked memory the device can address (cudaHostAlloc, or
- * cudaHostRegister with mapping, e.g. a pinned torch tensor) is read by the
- * first pass and written by the last pass directly, with no separate copies;
- * other memory is copied to a device buffer and back.  Device buffers come
- * from the library's pool. */
+ * cudaHostRegister with mapping, e.g. a pinned torch tensor): below 2^24 keys
+ * (or with one block) the first pass reads it and the last pass writes it
+ * directly, with no separate copies; from 2^24 keys the blocks are copied in
+ * groups on a library-created copy stream while earlier groups are
+ * block-sorted, and with exact splitting the result is copied back in
+ * partition ranges while later ranges merge (regular sampling: the final
+ * merge writes the host buffer directly).  Other memory is copied to a
+ * device buffer and back.  Device buffers come from the library's pool. */
 int ps_sort_host(void* host_keys, int64_t n, int dtype, int pivot_mode,
                  const ps_params* params, ps_stream_t stream);
 
