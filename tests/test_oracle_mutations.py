@@ -35,6 +35,11 @@ MUTANTS = {
     "merge_takes_larger": ("if (less(&lv[b].base[lv[b].pos], &lv[a].base[lv[a].pos])) return b;",
                            "if (less(&lv[a].base[lv[a].pos], &lv[b].base[lv[b].pos])) return b;"),
     "offsets_not_scanned": ("O[k + 1] = O[k] + t;", "O[k + 1] = t;"),
+    "psrs_sample_index_low": ("(unsigned __int128)j * (uint64_t)m", "(unsigned __int128)(j - 1) * (uint64_t)m"),
+    "pses_rank_not_clamped": ("int64_t want = r > 0 ? r : 1;", "int64_t want = r;"),
+    "pses_ties_not_counted": ("int64_t need = cc[k - 1] - taken;", "int64_t need = cc[k - 1];"),
+    "pses_below_counts_equal": ("below += count_lt(a + BLO(b), BHI(b) - BLO(b), pk[k - 1], pp[k - 1]);",
+                                "below += count_le(a + BLO(b), BHI(b) - BLO(b), pk[k - 1], pp[k - 1]);"),
     # the inverse order key that turns float pivots back into key bits
     "f32_pivot_branches_swapped": (
         "if (u & 0x80000000u) return (uint64_t)(u & 0x7fffffffu);\n        return (uint64_t)(uint32_t)~u;",
